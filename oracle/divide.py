@@ -1,0 +1,381 @@
+"""Plain references for the divide, border and merge steps (Alg. 1, Alg. 2).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Each function follows
+the paper's step in its own order and notation; numpy routines serve as
+single steps (a sort, a unique), nothing is blocked or fused.
+
+Readings of points the paper leaves open are stated next to each function.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import delaunay, nearest, predicates, edges as _edges
+
+MASK64 = (1 << 64) - 1
+
+
+# ---------------------------------------------------------------- sampling
+def splitmix64(x: int) -> int:
+    """One step of the SplitMix64 generator (Steele, Lea, Flood 2014):
+    advance by the golden-ratio increment, then the published finaliser."""
+    z = (x + 0x9E3779B97F4A7C15) & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def sample_size(n: int, frac: float, D: int) -> int:
+    """eta(n): ceil(frac * n), or ceil(sqrt(n)) when frac == 0 (the paper's
+    default, Sec. 4.1); at least D + 2 and at most n."""
+    eta = math.ceil(math.sqrt(n)) if frac <= 0 else math.ceil(frac * n)
+    return int(min(n, max(D + 2, eta)))
+
+
+def sample_keys(n: int, seed: int) -> np.ndarray:
+    s = splitmix64(seed & MASK64)
+    return np.array([splitmix64(s ^ i) for i in range(n)], dtype=np.uint64)
+
+
+def sample_ids(n: int, eta: int, seed: int) -> np.ndarray:
+    """Alg. 2, line 1: eta distinct indices uniformly at random, realised as
+    the eta smallest (key_i, i) with key_i = splitmix64(splitmix64(seed) xor i).
+    Returned sorted by index."""
+    keys = sample_keys(n, seed)
+    order = np.lexsort((np.arange(n), keys))
+    return np.sort(order[:eta]).astype(np.int64)
+
+
+# ---------------------------------------------------------------- graph
+WEIGHTS = ("log", "constant", "inverse", "linear")
+
+
+def edge_weights(PS: np.ndarray, E: np.ndarray, kind: str = "log") -> np.ndarray:
+    """Table 1 edge weights on the normalised length d = |v - w| / d*, with d*
+    the diagonal of the sample's bounding box, scaled to integers (the
+    partitioner works on integer weights): w = max(1, round(1000 * omega));
+    the inverse weight is capped at 1e6."""
+    lo, hi = PS.min(axis=0), PS.max(axis=0)
+    ext = hi - lo
+    dstar = math.sqrt(float(np.sum(ext * ext)))
+    diff = PS[E[:, 0]] - PS[E[:, 1]]
+    sq = diff[:, 0] * diff[:, 0]
+    for c in range(1, PS.shape[1]):
+        sq = sq + diff[:, c] * diff[:, c]
+    d = np.sqrt(sq) / dstar
+    if kind == "log":
+        om = -np.log(d)
+    elif kind == "constant":
+        om = np.ones_like(d) / 1000.0
+    elif kind == "inverse":
+        om = np.minimum(1.0 / d, 1e6)
+    elif kind == "linear":
+        om = 1.0 - d
+    else:
+        raise ValueError(kind)
+    return np.maximum(1, np.rint(1000.0 * om)).astype(np.int64)
+
+
+def sample_graph(PS: np.ndarray, gidS: np.ndarray, kind: str = "log"):
+    """Alg. 2, lines 2-3: T = DT(P_S); G = (V = P_S, E = edges of T, omega).
+    Returns (E (m,2) in sample positions, sorted, u < v; weights)."""
+    T = delaunay(PS, gidS)
+    pos = {int(g): i for i, g in enumerate(gidS)}
+    local = np.vectorize(pos.get)(T) if len(T) else T
+    E = _edges(local)
+    return E.astype(np.int64), edge_weights(PS, E, kind)
+
+
+# ---------------------------------------------------------------- partition
+def hilbert_key(q: np.ndarray, bits: int) -> int:
+    """Hilbert index of integer coordinates q (each < 2^bits), following
+    Skilling's transpose construction (AIP Conf. Proc. 707, 2004)."""
+    X = [int(v) for v in q]
+    n = len(X)
+    M = 1 << (bits - 1)
+    Q = M
+    while Q > 1:
+        P = Q - 1
+        for i in range(n):
+            if X[i] & Q:
+                X[0] ^= P
+            else:
+                t = (X[0] ^ X[i]) & P
+                X[0] ^= t
+                X[i] ^= t
+        Q >>= 1
+    for i in range(1, n):
+        X[i] ^= X[i - 1]
+    t = 0
+    Q = M
+    while Q > 1:
+        if X[n - 1] & Q:
+            t ^= Q - 1
+        Q >>= 1
+    for i in range(n):
+        X[i] ^= t
+    key = 0
+    for b in range(bits - 1, -1, -1):
+        for i in range(n):
+            key = (key << 1) | ((X[i] >> b) & 1)
+    return key
+
+
+def hilbert_bits(D: int) -> int:
+    return 16 if D == 2 else 10
+
+
+def quantize(PS: np.ndarray, bits: int) -> np.ndarray:
+    lo, hi = PS.min(axis=0), PS.max(axis=0)
+    out = np.zeros(PS.shape, dtype=np.int64)
+    for c in range(PS.shape[1]):
+        if hi[c] > lo[c]:
+            w = (PS[:, c] - lo[c]) / (hi[c] - lo[c]) * float(1 << bits)
+            out[:, c] = np.minimum((1 << bits) - 1, np.floor(w)).astype(np.int64)
+    return out
+
+
+def partition_bounds(eta: int, k: int, eps: float):
+    """|V_i| <= (1 + eps) ceil(|V| / k) (Sec. 3); a floor of
+    max(1, floor((1 - eps) |V| / k)) keeps every block non-empty."""
+    ideal = math.ceil(eta / k)
+    lmax = int(math.floor((1.0 + eps) * ideal))
+    lmin = max(1, int(math.floor((1.0 - eps) * eta / k)))
+    return lmin, lmax
+
+
+def partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float = 0.05,
+              rounds: int = 16) -> np.ndarray:
+    """Size-constrained k-way partition of the sample graph (stands in for
+    KaHIP, which is not available).  Deterministic:
+
+    1. initial blocks: sample vertices in Hilbert order (ties: vertex index)
+       cut into k consecutive runs, block = floor(rank * k / eta);
+    2. `rounds` rounds of synchronous label propagation.  In round r only
+       vertices with v % 2 == r % 2 move.  A vertex's target is the
+       neighbouring block with the largest total edge weight to it (ties:
+       smaller block), if that beats its own block.  Candidates are taken in
+       vertex order: the j-th candidate into block b is accepted if
+       j < Lmax - |V_b| and, as the j'-th candidate leaving its block a,
+       j' < |V_a| - Lmin.
+    """
+    eta, D = PS.shape
+    if k <= 1:
+        return np.zeros(eta, dtype=np.int64)
+    bits = hilbert_bits(D)
+    q = quantize(PS, bits)
+    keys = np.array([hilbert_key(q[i], bits) for i in range(eta)], dtype=np.int64)
+    order = np.lexsort((np.arange(eta), keys))
+    block = np.empty(eta, dtype=np.int64)
+    block[order] = (np.arange(eta) * k) // eta
+    lmin, lmax = partition_bounds(eta, k, eps)
+    # adjacency lists with weights
+    nbrs = [[] for _ in range(eta)]
+    for (u, v), ww in zip(E, w):
+        nbrs[u].append((v, int(ww)))
+        nbrs[v].append((u, int(ww)))
+    for r in range(rounds):
+        size = np.bincount(block, minlength=k)
+        target = np.full(eta, -1, dtype=np.int64)
+        for v in range(eta):
+            if v % 2 != r % 2:
+                continue
+            conn = {}
+            for u, ww in nbrs[v]:
+                conn[block[u]] = conn.get(block[u], 0) + ww
+            own = conn.get(block[v], 0)
+            best, bw = -1, -1
+            for b in sorted(conn):
+                if b != block[v] and conn[b] > bw:
+                    best, bw = b, conn[b]
+            if best >= 0 and bw > own:
+                target[v] = best
+        cnt_in = np.zeros(k, dtype=np.int64)
+        cnt_out = np.zeros(k, dtype=np.int64)
+        moves = []
+        for v in range(eta):
+            t = target[v]
+            if t < 0:
+                continue
+            a = block[v]
+            if cnt_in[t] < lmax - size[t] and cnt_out[a] < size[a] - lmin:
+                moves.append((v, t))
+            cnt_in[t] += 1
+            cnt_out[a] += 1
+        for v, t in moves:
+            block[v] = t
+    return block
+
+
+def cut_weight(E: np.ndarray, w: np.ndarray, block: np.ndarray) -> int:
+    """Sec. 4.6: total weight of edges whose ends lie in different blocks."""
+    return int(w[block[E[:, 0]] != block[E[:, 1]]].sum())
+
+
+# ---------------------------------------------------------------- labels
+def labels(P: np.ndarray, PS: np.ndarray, gidS: np.ndarray, block: np.ndarray,
+           idx: np.ndarray | None = None) -> np.ndarray:
+    """Alg. 2, lines 6-8: each point takes the block of its nearest sample
+    point (exact squared distance; ties: smaller global index).  `idx`
+    restricts the computation to a subset of points."""
+    Q = P if idx is None else P[idx]
+    nn = nearest(Q, PS, gidS)
+    return block[nn]
+
+
+# ---------------------------------------------------------------- kd divide
+def kd_labels(P: np.ndarray, k: int) -> np.ndarray:
+    """The original divide (Sec. 2.3, strategy ii): recursive median splits
+    with the splitting dimension chosen cyclically.  A node holding m points
+    and kk leaves sends floor(m * floor(kk/2) / kk) points with the smallest
+    (coordinate, index) to the left child.  Leaves are numbered left to right."""
+    n, D = P.shape
+    lab = np.zeros(n, dtype=np.int64)
+
+    def rec(ids, kk, depth, first):
+        if kk == 1:
+            lab[ids] = first
+            return
+        c = depth % D
+        order = np.lexsort((ids, P[ids, c]))
+        ids = ids[order]
+        kl = kk // 2
+        ml = (len(ids) * kl) // kk
+        rec(ids[:ml], kl, depth + 1, first)
+        rec(ids[ml:], kk - kl, depth + 1, first + kl)
+
+    rec(np.arange(n), k, 0, 0)
+    return lab
+
+
+# ---------------------------------------------------------------- border
+def partial_triangulations(P: np.ndarray, lab: np.ndarray, k: int):
+    """T_i = DT(P_i) with global indices (Alg. 1, line 5); also returns the
+    raw meshes (local ids, -1 = infinite vertex) for the ghost simplices."""
+    out = []
+    for i in range(k):
+        ids = np.nonzero(lab == i)[0]
+        if len(ids) <= P.shape[1]:
+            out.append((ids, None, None))
+            continue
+        try:
+            T, v, nb = delaunay(P[ids], ids, mesh=True)
+        except Exception:
+            out.append((ids, None, None))       # degenerate partition
+            continue
+        out.append((ids, T, v))
+    return out
+
+
+def border_exact(P: np.ndarray, lab: np.ndarray, k: int):
+    """Alg. 1, lines 7-18 with the exact primitive and every simplex tested
+    (a superset of what a breadth-first search from the hull reaches).
+
+    A finite simplex of T_i is a border simplex iff its perturbed circumsphere
+    contains a point of another partition.  A ghost simplex (hull facet f of
+    T_i) is a border simplex iff some point of another partition is in
+    conflict with it (strictly beyond f, or on f's hyperplane and inside f's
+    circumsphere).  A partition too small or too flat to triangulate
+    contributes all its points.  Returns (set of border finite simplices as
+    sorted gid tuples, sorted array vertices(B))."""
+    n, D = P.shape
+    parts = partial_triangulations(P, lab, k)
+    Bset = set()
+    VB = set()
+    for i, (ids, T, v) in enumerate(parts):
+        if T is None:
+            VB.update(int(x) for x in ids)
+            continue
+        others = np.nonzero(lab != i)[0]
+        # all points, global indexing; test every simplex of the raw mesh
+        for row in v:
+            if (row == -1).any():
+                g = int(np.nonzero(row == -1)[0][0])
+                fin = ids[row[row >= 0]]
+                hit = False
+                for q in others:
+                    tup = [int(ids[x]) if x >= 0 else -1 for x in row]
+                    tup[g] = int(q)
+                    o = predicates(P, "orient", np.array([tup], dtype=np.int32))[0]
+                    if o > 0:
+                        hit = True
+                        break
+                    if o == 0 and _coplanar_conflict(P, fin, q):
+                        hit = True
+                        break
+                if hit:
+                    VB.update(int(x) for x in fin)
+            else:
+                s = ids[row]
+                tup = np.concatenate([np.repeat(s[None, :], len(others), axis=0),
+                                      others[:, None]], axis=1).astype(np.int32)
+                r = predicates(P, "insphere", tup)
+                if np.any(r > 0):
+                    Bset.add(tuple(sorted(int(x) for x in s)))
+                    VB.update(int(x) for x in s)
+    return Bset, np.array(sorted(VB), dtype=np.int64), parts
+
+
+def _coplanar_conflict(P, fin, q) -> bool:
+    """q on the hyperplane of hull facet `fin`: inside the facet's own
+    circumsphere.  Decided through the full-dimensional DT of the facet plus
+    q (q creates a facet-simplex containing it) -- tiny brute force."""
+    D = P.shape[1]
+    if D == 2:
+        a, b, x = P[fin[0]], P[fin[1]], P[q]
+        return float(np.dot(a - x, b - x)) < 0
+    # 3D: q coplanar with triangle fin: inside its circumcircle iff q lies in
+    # the circumball of (fin, any off-plane point); the perturbed test of the
+    # C oracle covers exact cocircularity, reached here through predicates
+    # with an auxiliary point appended.
+    a = P[fin[0]]
+    n = np.cross(P[fin[1]] - a, P[fin[2]] - a)
+    k = int(np.argmax(np.abs(n)))
+    aux = a.copy()
+    aux[k] = a[k] + (abs(a[k]) + 1.0)
+    Q = np.vstack([P[list(fin)], aux[None, :], P[q][None, :]])
+    o = predicates(Q, "orient", np.array([[0, 1, 2, 3]], dtype=np.int32))[0]
+    r = predicates(Q, "insphere_raw", np.array([[0, 1, 2, 3, 4]], dtype=np.int32))[0] * o
+    if r != 0:
+        return r > 0
+    raise NotImplementedError("exactly cocircular coplanar hull case")
+
+
+# ---------------------------------------------------------------- merge
+def merge(parts, Bset, VB, P, lab):
+    """Alg. 1, lines 19-28: T = (U T_i) minus B; add s_b in T_B = DT(vertices(B))
+    if its vertices lie in more than one partition, or if it equals a border
+    simplex.  Returns the merged simplices as a sorted (m, d+1) array."""
+    D = P.shape[1]
+    T = set()
+    for ids, Ti, _ in parts:
+        if Ti is None:
+            continue
+        for s in Ti:
+            t = tuple(int(x) for x in s)
+            if t not in Bset:
+                T.add(t)
+    if len(VB) > D:
+        TB = delaunay(P[VB], VB)
+        for s in TB:
+            t = tuple(int(x) for x in s)
+            if len(set(int(lab[x]) for x in t)) > 1 or t in Bset:
+                T.add(t)
+    out = np.array(sorted(T), dtype=np.int64).reshape(-1, D + 1)
+    return out
+
+
+# ---------------------------------------------------------------- metrics
+def metrics(sizes: np.ndarray, n: int, eta: int, nVB: int) -> dict:
+    """Sec. 4.6: deviation p_i / (N/k) - 1 (max reported as imbalance),
+    coefficient of variation with the k-1 denominator, and the
+    overtriangulation factor o_DT = (|P| + |P_S| + |vertices(B)|) / |P|."""
+    sizes = np.asarray(sizes, dtype=np.float64)
+    k = len(sizes)
+    mu = sizes.sum() / k
+    dev = sizes / (n / k) - 1.0
+    cv = math.sqrt(((sizes - mu) ** 2).sum() / (k - 1)) / mu if k > 1 else 0.0
+    return dict(imbalance=float(dev.max()), min_deviation=float(dev.min()), cv=float(cv),
+                o_dt=(n + eta + nVB) / n)

@@ -1,0 +1,165 @@
+"""Pins for the divide / border / merge references (Alg. 1 and Alg. 2).
+
+The strongest pin: running the paper's merge (Alg. 1, lines 19-28) on the
+exact border set reproduces DT(P) exactly, for sample-based and kd labels,
+and stays exact when the border set is enlarged arbitrarily (a conservative
+intersection primitive only ever adds simplices).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import pointsets
+from oracle import divide as dv
+
+
+def test_splitmix64_published_vector():
+    # First output of SplitMix64 seeded with 0 (published reference value).
+    assert dv.splitmix64(0) == 0xE220A8397B1DCDAF
+
+
+def test_sample_ids_definition():
+    n, eta = 5000, 50
+    s = dv.sample_ids(n, eta, 7)
+    assert len(s) == eta and len(np.unique(s)) == eta and np.all(np.diff(s) > 0)
+    assert s.min() >= 0 and s.max() < n
+    # different seeds give different samples; same seed the same
+    assert not np.array_equal(s, dv.sample_ids(n, eta, 8))
+    assert np.array_equal(s, dv.sample_ids(n, eta, 7))
+    assert dv.sample_size(10000, 0.01, 2) == 100
+    assert dv.sample_size(10000, 0.0, 3) == 100
+    assert dv.sample_size(10, 0.01, 3) == 5
+
+
+def test_sample_is_roughly_uniform():
+    n = 4000
+    hits = np.zeros(n)
+    for seed in range(200):
+        hits[dv.sample_ids(n, 40, seed)] += 1
+    # each index is drawn with probability 40/4000 per seed -> mean 2
+    assert abs(hits.mean() - 2.0) < 1e-9
+    assert hits[: n // 2].sum() / hits.sum() == pytest.approx(0.5, abs=0.05)
+
+
+@pytest.mark.parametrize("bits,D", [(3, 2), (2, 3), (4, 2)])
+def test_hilbert_key_is_a_hilbert_curve(bits, D):
+    """Keys form a permutation of the cells and consecutive cells are face
+    neighbours (the defining property of a Hilbert curve)."""
+    cells = list(itertools.product(range(1 << bits), repeat=D))
+    keys = [dv.hilbert_key(np.array(c), bits) for c in cells]
+    assert sorted(keys) == list(range(len(cells)))
+    order = [c for _, c in sorted(zip(keys, cells))]
+    for a, b in zip(order, order[1:]):
+        assert sum(abs(x - y) for x, y in zip(a, b)) == 1
+
+
+def test_graph_is_sample_dt_edges(orc):
+    P = pointsets.uniform(2000, 2, 3)
+    ids = dv.sample_ids(2000, 60, 1)
+    E, w = dv.sample_graph(P[ids], ids)
+    T = orc.bruteforce(P[ids])
+    assert np.array_equal(E, orc.edges(T))
+    h = orc.hull_vertex_count(T)
+    assert len(E) == 3 * 60 - 3 - h
+    # Table 1 log weight: -ln(|v-w| / d*), scaled by 1000, at least 1
+    PS = P[ids]
+    dstar = np.linalg.norm(PS.max(0) - PS.min(0))
+    d = np.linalg.norm(PS[E[:, 0]] - PS[E[:, 1]], axis=1) / dstar
+    assert np.all(np.abs(w - np.maximum(1, np.rint(-1000 * np.log(d)))) == 0)
+    assert np.all(w >= 1)
+
+
+@pytest.mark.parametrize("D,k", [(2, 4), (2, 7), (3, 16)])
+def test_partition_balance_and_cut(orc, D, k):
+    P = pointsets.clustered(3000, 5) if D == 3 else pointsets.normal(3000, 2, 5)
+    ids = dv.sample_ids(3000, 400, 2)
+    PS = P[ids]
+    E, w = dv.sample_graph(PS, ids)
+    b0 = dv.partition(PS, E, w, k, rounds=0)
+    b = dv.partition(PS, E, w, k)
+    lmin, lmax = dv.partition_bounds(400, k, 0.05)
+    sizes = np.bincount(b, minlength=k)
+    assert sizes.max() <= lmax and sizes.min() >= lmin
+    assert dv.cut_weight(E, w, b) <= dv.cut_weight(E, w, b0)
+    assert np.array_equal(b, dv.partition(PS, E, w, k))
+
+
+def test_kd_labels_are_median_boxes():
+    P = pointsets.clustered(1000, 9)
+    lab = dv.kd_labels(P, 8)
+    sizes = np.bincount(lab, minlength=8)
+    assert sizes.max() - sizes.min() <= 1
+    # first split on x: leaves 0-3 lie left of leaves 4-7
+    assert P[lab < 4, 0].max() <= P[lab >= 4, 0].min()
+    assert P[lab < 2, 1].max() <= P[(lab >= 2) & (lab < 4), 1].min()
+    lab5 = dv.kd_labels(P, 5)
+    assert np.bincount(lab5).sum() == 1000 and len(np.unique(lab5)) == 5
+
+
+def test_labels_are_nearest_sample_block():
+    P = pointsets.uniform(3000, 3, 4)
+    ids = dv.sample_ids(3000, 80, 3)
+    block = np.arange(80) % 5
+    lab = dv.labels(P, P[ids], ids, block)
+    d = ((P[:, None, :] - P[ids][None, :, :]) ** 2).sum(-1)
+    assert np.array_equal(lab, block[np.argmin(d, axis=1)])
+    assert np.all(lab[ids] == block)
+
+
+def test_metrics_values():
+    m = dv.metrics(np.array([90, 110, 100, 100]), 400, 10, 30)
+    assert m["imbalance"] == pytest.approx(0.1)
+    assert m["min_deviation"] == pytest.approx(-0.1)
+    assert m["cv"] == pytest.approx(math.sqrt(200 / 3) / 100)
+    assert m["o_dt"] == pytest.approx(440 / 400)
+
+
+def _sample_labels(P, k, frac, seed):
+    n, D = P.shape
+    eta = dv.sample_size(n, frac, D)
+    ids = dv.sample_ids(n, eta, seed)
+    E, w = dv.sample_graph(P[ids], ids)
+    block = dv.partition(P[ids], E, w, k)
+    return dv.labels(P, P[ids], ids, block)
+
+
+@pytest.mark.parametrize("D,n,k,kind", [(2, 400, 4, "sample"), (2, 300, 5, "kd"),
+                                        (3, 160, 3, "sample"), (3, 160, 4, "kd")])
+def test_divide_and_conquer_reproduces_dt(orc, D, n, k, kind):
+    P = pointsets.uniform(n, D, 17) if D == 2 else pointsets.clustered(n, 17)
+    lab = _sample_labels(P, k, 0.1, 3) if kind == "sample" else dv.kd_labels(P, k)
+    Bset, VB, parts = dv.border_exact(P, lab, k)
+    assert 0 < len(VB) < n
+    T = dv.merge(parts, Bset, VB, P, lab)
+    assert np.array_equal(T, orc.delaunay(P))
+
+
+def test_merge_is_exact_for_any_border_superset(orc):
+    P = pointsets.normal(300, 2, 23)
+    lab = dv.kd_labels(P, 4)
+    Bset, VB, parts = dv.border_exact(P, lab, 4)
+    rng = np.random.default_rng(0)
+    want = orc.delaunay(P)
+    for trial in range(3):
+        B2 = set(Bset)
+        for ids, T, _ in parts:
+            pick = rng.random(len(T)) < 0.15
+            B2.update(tuple(int(x) for x in s) for s in T[pick])
+        VB2 = np.array(sorted(set(VB.tolist()) | {x for s in B2 for x in s}), dtype=np.int64)
+        assert np.array_equal(dv.merge(parts, B2, VB2, P, lab), want)
+
+
+def test_degenerate_partition_contributes_all_points(orc):
+    """A partition holding only collinear points cannot be triangulated; all
+    of its points join the border set and the merge stays exact."""
+    P = pointsets.uniform(120, 2, 2)
+    line = np.stack([np.linspace(0.1, 0.9, 6), np.full(6, 0.123456)], axis=1)
+    P = np.vstack([P, line])
+    lab = np.zeros(len(P), dtype=np.int64)
+    lab[P[:, 0] > 0.5] = 1
+    lab[120:] = 2
+    Bset, VB, parts = dv.border_exact(P, lab, 3)
+    assert set(range(120, 126)) <= set(VB.tolist())
+    assert np.array_equal(dv.merge(parts, Bset, VB, P, lab), orc.delaunay(P))
