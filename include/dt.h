@@ -1,0 +1,197 @@
+/*
+ * dt.h -- C ABI of the GB300 sample-based divide-and-conquer Delaunay
+ * triangulation (Funke, Sanders, Winkler: "Load-Balancing for Parallel
+ * Delaunay Triangulations").
+ *
+ * What is computed (Sec. 2.1): DT(P) for a point set P in R^2 or R^3 -- the
+ * triangulation of conv(P) whose vertex set is P and in which no point lies
+ * inside the circumsphere of any simplex.  Ties (cocircular / cospherical
+ * subsets) are resolved by a symbolic perturbation of the lifting map that
+ * ranks points by their input index, so the result is unique for every
+ * duplicate-free input and does not depend on k, the sample or the seed.
+ *
+ * How (Alg. 1 with the divide step of Alg. 2): sample eta points, triangulate
+ * them, partition the sample's Delaunay graph into k balanced blocks, label
+ * every point with the block of its nearest sample point, triangulate the k
+ * partitions independently, detect border simplices whose circumsphere may
+ * reach another partition, triangulate the border vertices, and merge with
+ * hash-table lookups.  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Return value: 0 on success, a negative DT_E_* code otherwise.  No call
+ *     aborts the process; after an error the context stays usable and
+ *     dt_last_error() describes the failure.
+ *   - Pointers marked "host or device" may point to host memory or to device
+ *     memory of the context's GPU; the library detects which.
+ *   - Points are float64, row-major (n x dim).  Indices are 0-based input
+ *     order.  Simplices are returned as int32 vertex indices, each tuple
+ *     sorted ascending, the whole array sorted lexicographically; only
+ *     finite simplices are returned.
+ *   - The library owns its results until the next dt_triangulate on the same
+ *     context or dt_destroy.  The caller owns every buffer it passes.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GB300_DT_H
+#define GB300_DT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DT_API __attribute__((visibility("default")))
+#else
+#define DT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DT_OK 0
+#define DT_E_ARG (-1)        /* invalid argument (null, dim, n, k, frac, non-finite) */
+#define DT_E_DUPLICATE (-2)  /* two input points coincide exactly */
+#define DT_E_DEGENERATE (-3) /* all points lie on one line (2D) or plane (3D) */
+#define DT_E_NOMEM (-4)      /* device allocation failed or budget exceeded */
+#define DT_E_TIMEOUT (-5)    /* a device loop hit its iteration limit */
+#define DT_E_OVERFLOW (-6)   /* an internal arena or table ran out of room */
+#define DT_E_CUDA (-7)       /* a CUDA runtime call failed */
+#define DT_E_RANGE (-8)      /* coordinates span too many binary orders of magnitude
+                                for the exact fallback (> ~200 bits between the
+                                largest coordinate difference and the finest bit) */
+#define DT_E_INTERNAL (-9)   /* consistency check failed (a bug) */
+
+/* Divide strategies. */
+#define DT_DIVIDE_SAMPLE 0   /* Alg. 2: sample DT + graph partition + nearest-sample labels */
+#define DT_DIVIDE_KD 1       /* Sec. 2.3: recursive median split, cyclic dimension */
+
+/* Border-detection primitives (Sec. 3.2). */
+#define DT_PRIM_GRID 0       /* occupied uniform-grid cells with a coarse-to-fine hierarchy */
+#define DT_PRIM_BBOX 1       /* one axis-aligned bounding box per partition */
+
+/* Edge weights of the sample graph (Table 1). */
+#define DT_WEIGHT_LOG 0
+#define DT_WEIGHT_CONSTANT 1
+#define DT_WEIGHT_INVERSE 2
+#define DT_WEIGHT_LINEAR 3
+
+typedef struct dt_config {
+  int divide;            /* DT_DIVIDE_*; default DT_DIVIDE_SAMPLE */
+  int primitive;         /* DT_PRIM_*; default DT_PRIM_GRID */
+  int weight;            /* DT_WEIGHT_*; default DT_WEIGHT_LOG (Sec. 4.3) */
+  int lp_rounds;         /* label-propagation rounds of the partitioner; default 16 */
+  double epsilon;        /* partition imbalance, |V_i| <= (1+eps) ceil(|V|/k); default 0.05 */
+  double grid_cell;      /* c_G: grid cell edge in units of the mean point spacing; default 1 */
+  uint64_t seed;         /* sample seed; default 1 */
+  int base_threshold;    /* N of Alg. 1: run k = 1 when n / k < N; default 2048 */
+  int validate;          /* 1: check every interior facet is locally Delaunay after the merge */
+  int cavity_cap;        /* initial per-insertion cavity capacity (simplices); default 64 */
+  int reserved[8];
+} dt_config;
+
+typedef struct dt_stats {
+  int64_t n;             /* input points */
+  int64_t simplices;     /* finite simplices in the result */
+  int32_t k;             /* partitions used (1 when the base case ran) */
+  int32_t dim;
+  int64_t eta;           /* sample size */
+  int64_t border_vertices;   /* |vertices(B)| */
+  int64_t border_simplices;  /* |B| */
+  int64_t border_dt_simplices; /* |T_B| (finite) */
+  double imbalance;      /* max_i p_i / (n/k) - 1 (Sec. 4.6) */
+  double cv;             /* coefficient of variation of partition sizes, k-1 denominator */
+  double o_dt;           /* overtriangulation factor (n + eta + |vertices(B)|) / n */
+  int64_t cut_weight;    /* weight of sample-graph edges cut by the partition */
+  int32_t rounds_max;    /* insertion rounds of the slowest triangulation */
+  int32_t exact_calls;   /* exact-arithmetic fallbacks taken (saturating) */
+  double ms_total;       /* device time of the whole call, ms */
+  double ms_phase[8];    /* sample+graph, partition+label+scatter, partial DTs, border,
+                            border DT, merge, canonicalise, validate */
+  int64_t partition_size_max;
+  int64_t partition_size_min;
+} dt_stats;
+
+typedef struct dt_ctx dt_ctx;
+
+/* Fill *cfg with the defaults listed in dt_config.  Returns DT_OK. */
+DT_API int dt_config_default(dt_config* cfg);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t,
+ * may be NULL for a private stream) is the stream every kernel of this
+ * context runs on; `cfg` may be NULL for defaults.  *out receives the
+ * context (owned by the caller, released by dt_destroy). */
+DT_API int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg);
+
+/* Replace the context's configuration (NULL restores the defaults). */
+DT_API int dt_set_config(dt_ctx* ctx, const dt_config* cfg);
+
+/* Triangulate n points of dimension dim (2 or 3), points host or device,
+ * with k partitions (k >= 1; k = 1 triangulates directly) and sample
+ * fraction sample_frac in [0, 1] (0 selects the paper's default
+ * eta = ceil(sqrt(n)), Sec. 4.1).  Device points must stay valid until the
+ * call returns.  The result replaces the context's previous result.
+ * Errors: DT_E_ARG, DT_E_DUPLICATE, DT_E_DEGENERATE, DT_E_NOMEM,
+ * DT_E_TIMEOUT, DT_E_OVERFLOW, DT_E_RANGE, DT_E_CUDA, DT_E_INTERNAL. */
+DT_API int dt_triangulate(dt_ctx* ctx, const double* points, int64_t n, int dim, int k,
+                   double sample_frac);
+
+/* Copy the finite simplices of the last result into out (host or device,
+ * room for capacity simplices of dim+1 int32 each).  *count receives the
+ * number of simplices; with out == NULL only *count is written.  Returns
+ * DT_E_ARG if capacity is too small. */
+DT_API int dt_get_simplices(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Device pointer to the last result's simplex array (library-owned, valid
+ * until the next dt_triangulate or dt_destroy) and its count. */
+DT_API int dt_get_simplices_device(dt_ctx* ctx, const int32_t** dptr, int64_t* count);
+
+/* Statistics of the last call. */
+DT_API int dt_get_stats(dt_ctx* ctx, dt_stats* stats);
+
+/* Per-point partition label of the last call (host or device out, n int32).
+ * All zeros when k = 1 ran. */
+DT_API int dt_get_labels(dt_ctx* ctx, int32_t* out, int64_t n);
+
+/* Sample of the last call: eta input indices, ascending (host or device out).
+ * *count receives eta; with out == NULL only *count is written. */
+DT_API int dt_get_sample(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Block of every sample point (eta int32, host or device out). */
+DT_API int dt_get_sample_blocks(dt_ctx* ctx, int32_t* out, int64_t capacity);
+
+/* Border vertices of the last call: |vertices(B)| input indices, ascending. */
+DT_API int dt_get_border_vertices(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Human-readable description of the last error on this context (never NULL). */
+DT_API const char* dt_last_error(dt_ctx* ctx);
+
+/* Release the context and every buffer it owns.  NULL is ignored. */
+DT_API void dt_destroy(dt_ctx* ctx);
+
+/* ---- step-level entry points (operate on caller buffers; host or device) ---- */
+
+/* Exact predicate signs for m index tuples into points (n x dim, host or
+ * device); gid (n int64, may be NULL for 0..n-1) ranks the perturbation.
+ * kind 0: orient of dim+1 points; 1: perturbed insphere of point dim+1
+ * against simplex 0..dim (orientation normalised, 0 if flat); 2: raw
+ * insphere sign (-1)^dim det[p_i - q, |p_i - q|^2]; 3: sign(|p-a|^2 - |p-b|^2)
+ * for tuples (p, a, b).  out: m int8 (host or device).  Runs on the GPU. */
+DT_API int dt_eval_predicates(dt_ctx* ctx, const double* points, int64_t n, int dim,
+                       const int64_t* gid, int kind, const int32_t* tuples, int64_t m,
+                       int8_t* out);
+
+/* Alg. 2, lines 6-8 on given inputs: label every point of P (n x dim) with
+ * block[j] of its exactly nearest sample point S_j (ties: smaller srank),
+ * walking the Delaunay graph of S.  All buffers host or device; out n int32. */
+DT_API int dt_label_points(dt_ctx* ctx, const double* P, int64_t n, int dim, const double* S,
+                    const int64_t* srank, const int32_t* block, int64_t m, int32_t* out);
+
+/* k-way partition of a sample graph given as an edge list (E rows u < v,
+ * int64 weights) over eta vertices with coordinates S (eta x dim): the
+ * deterministic Hilbert-runs + label-propagation partitioner.  out: eta int32. */
+DT_API int dt_partition_graph(dt_ctx* ctx, const double* S, int64_t eta, int dim, const int32_t* E,
+                       const int64_t* w, int64_t m, int k, double eps, int rounds,
+                       int32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_DT_H */

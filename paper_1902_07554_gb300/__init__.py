@@ -1,0 +1,267 @@
+"""GB300 sample-based divide-and-conquer Delaunay triangulation.
+
+A thin ctypes binding over the C ABI in include/dt.h.  Every step of the
+triangulation runs in the CUDA library ``_build/libgb300dt.so``; this module
+only marshals arguments.  There is no CPU fallback: if the library is missing
+or no CUDA device is visible, the calls raise.
+
+Typical use::
+
+    from paper_1902_07554_gb300 import Triangulator
+    with Triangulator() as tri:
+        simplices = tri.triangulate(points, k=16, sample_frac=0.005)
+        stats = tri.stats()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Triangulator", "DTError", "load_library", "declared_symbols", "Config", "Stats",
+           "DIVIDE_SAMPLE", "DIVIDE_KD", "PRIM_GRID", "PRIM_BBOX"]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(HERE), "include", "dt.h")
+
+DIVIDE_SAMPLE, DIVIDE_KD = 0, 1
+PRIM_GRID, PRIM_BBOX = 0, 1
+WEIGHTS = {"log": 0, "constant": 1, "inverse": 2, "linear": 3}
+
+ERRORS = {-1: "DT_E_ARG", -2: "DT_E_DUPLICATE", -3: "DT_E_DEGENERATE", -4: "DT_E_NOMEM",
+          -5: "DT_E_TIMEOUT", -6: "DT_E_OVERFLOW", -7: "DT_E_CUDA", -8: "DT_E_RANGE",
+          -9: "DT_E_INTERNAL"}
+
+
+class DTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("divide", ctypes.c_int), ("primitive", ctypes.c_int), ("weight", ctypes.c_int),
+                ("lp_rounds", ctypes.c_int), ("epsilon", ctypes.c_double),
+                ("grid_cell", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("base_threshold", ctypes.c_int), ("validate", ctypes.c_int),
+                ("cavity_cap", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("simplices", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("eta", ctypes.c_int64),
+                ("border_vertices", ctypes.c_int64), ("border_simplices", ctypes.c_int64),
+                ("border_dt_simplices", ctypes.c_int64), ("imbalance", ctypes.c_double),
+                ("cv", ctypes.c_double), ("o_dt", ctypes.c_double), ("cut_weight", ctypes.c_int64),
+                ("rounds_max", ctypes.c_int32), ("exact_calls", ctypes.c_int32),
+                ("ms_total", ctypes.c_double), ("ms_phase", ctypes.c_double * 8),
+                ("partition_size_max", ctypes.c_int64), ("partition_size_min", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if name == "ms_phase" else v
+        return d
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Names of the entry points declared in include/dt.h."""
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^DT_API\s+[\w\s\*]+?\b(dt_\w+)\s*\(", txt, flags=re.M)))
+
+
+def load_library(build: bool = True):
+    """Load (building first if needed) the CUDA library; raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    L = ctypes.CDLL(path)
+    p, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "dt_config_default": ([p], i32),
+        "dt_create": ([p, i32, p, p], i32),
+        "dt_set_config": ([p, p], i32),
+        "dt_triangulate": ([p, p, i64, i32, i32, dbl], i32),
+        "dt_get_simplices": ([p, p, i64, p], i32),
+        "dt_get_simplices_device": ([p, p, p], i32),
+        "dt_get_stats": ([p, p], i32),
+        "dt_get_labels": ([p, p, i64], i32),
+        "dt_get_sample": ([p, p, i64, p], i32),
+        "dt_get_sample_blocks": ([p, p, i64], i32),
+        "dt_get_border_vertices": ([p, p, i64, p], i32),
+        "dt_last_error": ([p], ctypes.c_char_p),
+        "dt_destroy": ([p], None),
+        "dt_eval_predicates": ([p, p, i64, i32, p, i32, p, i64, p], i32),
+        "dt_label_points": ([p, p, i64, i32, p, p, p, i64, p], i32),
+        "dt_partition_graph": ([p, p, i64, i32, p, p, i64, i32, dbl, i32, p], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _as_points(points):
+    if hasattr(points, "data_ptr"):           # torch tensor (host or cuda)
+        t = points.contiguous()
+        if t.dtype != __import__("torch").float64:
+            raise TypeError("points must be float64")
+        return t, t.shape[0], t.shape[1]
+    a = np.ascontiguousarray(points, dtype=np.float64)
+    if a.ndim != 2:
+        raise ValueError("points must be (n, dim)")
+    return a, a.shape[0], a.shape[1]
+
+
+class Triangulator:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, stream=None, **config):
+        self.L = load_library()
+        self.ctx = ctypes.c_void_p()
+        cfg = self.default_config()
+        for k, v in config.items():
+            if k == "weight" and isinstance(v, str):
+                v = WEIGHTS[v]
+            setattr(cfg, k, v)
+        self._cfg = cfg
+        rc = self.L.dt_create(ctypes.byref(self.ctx), device, stream, ctypes.byref(cfg))
+        if rc:
+            raise DTError(rc, "dt_create failed (no CUDA device?)")
+
+    def default_config(self) -> Config:
+        cfg = Config()
+        self.L.dt_config_default(ctypes.byref(cfg))
+        return cfg
+
+    def configure(self, **config):
+        for k, v in config.items():
+            if k == "weight" and isinstance(v, str):
+                v = WEIGHTS[v]
+            setattr(self._cfg, k, v)
+        self._check(self.L.dt_set_config(self.ctx, ctypes.byref(self._cfg)))
+
+    def _check(self, rc):
+        if rc:
+            raise DTError(rc, self.L.dt_last_error(self.ctx).decode())
+
+    def close(self):
+        if self.ctx:
+            self.L.dt_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- main call
+    def triangulate(self, points, k: int = 1, sample_frac: float = 0.0, fetch: bool = True):
+        """DT(points): (m, dim+1) int32 array of input indices, rows sorted."""
+        P, n, dim = _as_points(points)
+        self._check(self.L.dt_triangulate(self.ctx, _ptr(P), n, dim, k, float(sample_frac)))
+        return self.simplices() if fetch else None
+
+    def simplices(self, out=None):
+        cnt = ctypes.c_int64()
+        self._check(self.L.dt_get_simplices(self.ctx, None, 0, ctypes.byref(cnt)))
+        s = self.stats()
+        if out is None:
+            out = np.empty((cnt.value, s.dim + 1), dtype=np.int32)
+        self._check(self.L.dt_get_simplices(self.ctx, _ptr(out), cnt.value, ctypes.byref(cnt)))
+        return out
+
+    def simplex_count(self) -> int:
+        cnt = ctypes.c_int64()
+        self._check(self.L.dt_get_simplices(self.ctx, None, 0, ctypes.byref(cnt)))
+        return cnt.value
+
+    def stats(self) -> Stats:
+        s = Stats()
+        self._check(self.L.dt_get_stats(self.ctx, ctypes.byref(s)))
+        return s
+
+    def labels(self):
+        n = self.stats().n
+        out = np.empty(n, dtype=np.int32)
+        self._check(self.L.dt_get_labels(self.ctx, _ptr(out), n))
+        return out
+
+    def sample(self):
+        cnt = ctypes.c_int64()
+        self._check(self.L.dt_get_sample(self.ctx, None, 0, ctypes.byref(cnt)))
+        out = np.empty(cnt.value, dtype=np.int32)
+        self._check(self.L.dt_get_sample(self.ctx, _ptr(out), cnt.value, ctypes.byref(cnt)))
+        return out
+
+    def sample_blocks(self):
+        eta = len(self.sample())
+        out = np.empty(eta, dtype=np.int32)
+        self._check(self.L.dt_get_sample_blocks(self.ctx, _ptr(out), eta))
+        return out
+
+    def border_vertices(self):
+        cnt = ctypes.c_int64()
+        self._check(self.L.dt_get_border_vertices(self.ctx, None, 0, ctypes.byref(cnt)))
+        out = np.empty(cnt.value, dtype=np.int32)
+        self._check(self.L.dt_get_border_vertices(self.ctx, _ptr(out), cnt.value, ctypes.byref(cnt)))
+        return out
+
+    # ------------------------------------------------------------- steps
+    def eval_predicates(self, points, kind: str, tuples, gid=None):
+        code = {"orient": 0, "insphere": 1, "insphere_raw": 2, "closer": 3}[kind]
+        P = np.ascontiguousarray(points, dtype=np.float64)
+        T = np.ascontiguousarray(tuples, dtype=np.int32)
+        g = None if gid is None else np.ascontiguousarray(gid, dtype=np.int64)
+        out = np.empty(len(T), dtype=np.int8)
+        self._check(self.L.dt_eval_predicates(self.ctx, _ptr(P), P.shape[0], P.shape[1], _ptr(g), code,
+                                              _ptr(T), len(T), _ptr(out)))
+        return out
+
+    def label_points(self, P, S, srank, block):
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        r = np.ascontiguousarray(srank, dtype=np.int64)
+        b = np.ascontiguousarray(block, dtype=np.int32)
+        out = np.empty(len(P), dtype=np.int32)
+        self._check(self.L.dt_label_points(self.ctx, _ptr(P), len(P), P.shape[1], _ptr(S), _ptr(r), _ptr(b),
+                                           len(S), _ptr(out)))
+        return out
+
+    def partition_graph(self, S, E, w, k, eps=0.05, rounds=16):
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        E = np.ascontiguousarray(E, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int64)
+        out = np.empty(len(S), dtype=np.int32)
+        self._check(self.L.dt_partition_graph(self.ctx, _ptr(S), len(S), S.shape[1], _ptr(E), _ptr(w), len(E),
+                                              k, float(eps), rounds, _ptr(out)))
+        return out

@@ -1,0 +1,67 @@
+// ctx.cuh -- the library context: stream, configuration, buffer pool, results.
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+struct dt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  dt_config cfg;
+  std::string err;
+  // named device buffers, grown on demand and reused across calls
+  struct Buf { void* p = nullptr; size_t cap = 0; };
+  std::map<std::string, Buf> pool;
+  gdt::DevStatus* status = nullptr;      // device status word
+  gdt::DevStatus* status_host = nullptr; // pinned mirror
+  int* counters_host = nullptr;          // pinned scratch for small read-backs (64 ints)
+  cudaEvent_t ev[16];
+  // last result
+  int dim = 0;
+  int64_t n = 0;
+  int32_t* out = nullptr;                // device, canonical simplices
+  int64_t nout = 0;
+  dt_stats stats;
+  std::vector<int32_t> h_labels_dummy;
+  // divide-step results of the last call (device)
+  int32_t* labels = nullptr;             // n
+  int32_t* sample = nullptr;             // eta (global ids, ascending)
+  int32_t* sample_block = nullptr;       // eta
+  int64_t eta = 0;
+  int32_t* border_vtx = nullptr;         // |V_B| global ids, ascending
+  int64_t n_border = 0;
+  gdt::EngineRun run_sample, run_parts, run_border;
+};
+
+namespace gdt {
+
+// Returns a device buffer of at least `bytes` bytes under `name`; contents
+// are undefined.  Returns nullptr on allocation failure.
+void* pool_get(dt_ctx* c, const std::string& name, size_t bytes);
+void pool_free_all(dt_ctx* c);
+
+int set_err(dt_ctx* c, int code, const std::string& msg);
+
+// Checks the device status word (synchronises the stream).  Returns 0 or a
+// DT_E_* code with the context's error message set.
+int check_status(dt_ctx* c, const char* where);
+
+// Generic device helpers (defined in util.cu).
+int exclusive_scan_i32(dt_ctx* c, const int* in, int* out, int64_t n, int* total_host);
+int exclusive_scan_i64(dt_ctx* c, const long long* in, long long* out, int64_t n);
+
+// Engine (engine.cu).
+int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,
+               int64_t npts, const std::vector<int64_t>& poff, const std::string& tag);
+
+// Canonicalisation of the finite live simplices of `run` whose instances are
+// selected: output rows (sorted gid tuples, lexicographic) into *out.
+// keep (optional, per slot) filters simplices.
+int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64_t nbuckets,
+                      int32_t** out, int64_t* nout, const std::string& tag);
+
+}  // namespace gdt

@@ -1,0 +1,529 @@
+// engine.cu -- batched parallel Bowyer-Watson insertion (see engine.cuh).
+#include <algorithm>
+#include <cstdio>
+
+#include "ctx.cuh"
+
+namespace gdt {
+
+constexpr int TAGBIT = (int)0x80000000;
+
+__device__ __forceinline__ unsigned long long mkkey(unsigned round, int p) {
+  return ((unsigned long long)round << 32) | (unsigned long long)fmix32((uint32_t)p);
+}
+__device__ __forceinline__ int get4(const int4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void set4(int4& v, int i, int x) {
+  if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ int* comp_ptr(int4* a, int s, int i) { return reinterpret_cast<int*>(a + s) + i; }
+
+// Appends `val` to list/counter for the lanes with pred set; every lane of
+// the warp must call this.
+__device__ __forceinline__ void warp_append(int* list, int* counter, bool pred, int val) {
+  unsigned mask = __ballot_sync(0xffffffffu, pred);
+  if (!mask) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) list[base + __popc(mask & ((1u << lane) - 1))] = val;
+}
+
+__device__ __forceinline__ bool collinear3(double4 a, double4 b, double4 c) {
+  double2 pa, pb, pc;
+  pa = make_double2(a.x, a.y); pb = make_double2(b.x, b.y); pc = make_double2(c.x, c.y);
+  if (orient2(pa, pb, pc) != 0) return false;
+  pa = make_double2(a.y, a.z); pb = make_double2(b.y, b.z); pc = make_double2(c.y, c.z);
+  if (orient2(pa, pb, pc) != 0) return false;
+  pa = make_double2(a.x, a.z); pb = make_double2(b.x, b.z); pc = make_double2(c.x, c.z);
+  return orient2(pa, pb, pc) == 0;
+}
+
+// Bounds guards: a corrupted link or vertex records an error instead of
+// touching memory outside the arena.
+template <int D>
+__device__ __forceinline__ bool slot_ok(const TriView<D>& T, int s) { return (unsigned)s < (unsigned)T.nslots; }
+template <int D>
+__device__ __forceinline__ bool verts_ok(const TriView<D>& T, const int4& v) {
+  bool ok = true;
+  for (int i = 0; i <= D; i++) {
+    int x = get4(v, i);
+    ok &= (x == INF_V) || ((unsigned)x < (unsigned)T.npts);
+  }
+  return ok;
+}
+
+template <int D>
+__device__ __forceinline__ int orient_tuple(const TriView<D>& T, const int4& v) {
+  int t[4] = {v.x, v.y, v.z, v.w};
+  return orient_p(T.pts, t);
+}
+
+// ---------------------------------------------------------------- init
+// One thread per instance: the first D+1 affinely independent points (in
+// index order) form a positively oriented simplex, surrounded by D+1 ghost
+// simplices (infinite vertex + one hull facet each).
+template <int D>
+__global__ void k_init(TriView<D> T, int ninst, const long long* poff, const int* toff, int* inst_status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ninst) return;
+  long long a = poff[i], b = poff[i + 1];
+  int base = toff[i];
+  T.tcount[i] = base;
+  if (b - a < D + 1) { inst_status[i] = 2; return; }
+  int pick[4];
+  int np = 0;
+  pick[np++] = (int)a;
+  for (long long q = a + 1; q < b && np < D + 1; q++) {
+    bool ok;
+    if (np == 1) {
+      ok = true;
+    } else if (D == 3 && np == 2) {
+      ok = !collinear3(reinterpret_cast<const double4*>(T.pts)[pick[0]],
+                       reinterpret_cast<const double4*>(T.pts)[pick[1]],
+                       reinterpret_cast<const double4*>(T.pts)[q]);
+    } else {
+      int t[4] = {pick[0], pick[1], pick[2], pick[3]};
+      t[np] = (int)q;
+      ok = orient_p(T.pts, t) != 0;
+    }
+    if (ok) pick[np++] = (int)q;
+  }
+  if (np < D + 1) { inst_status[i] = 1; return; }
+  int4 v0 = make_int4(pick[0], pick[1], pick[2], D == 3 ? pick[3] : -3);
+  if (orient_tuple(T, v0) < 0) { int t = v0.x; v0.x = v0.y; v0.y = t; }
+  int s0 = base;
+  T.tv[s0] = v0;
+  int4 g[4];
+  for (int k = 0; k <= D; k++) {
+    int4 gv = v0;
+    set4(gv, k, INF_V);
+    int x = (k + 1) % (D + 1), y = (k + 2) % (D + 1);
+    int tx = get4(gv, x), ty = get4(gv, y);
+    set4(gv, x, ty); set4(gv, y, tx);
+    g[k] = gv;
+    T.tv[s0 + 1 + k] = gv;
+  }
+  int4 n0 = make_int4(0, 0, 0, 0);
+  for (int k = 0; k <= D; k++) set4(n0, k, pack_nb(s0 + 1 + k, k));
+  T.tn[s0] = n0;
+  for (int k = 0; k <= D; k++) {
+    int4 nk = make_int4(0, 0, 0, 0);
+    for (int j = 0; j <= D; j++) {
+      int w = get4(g[k], j);
+      if (w == INF_V) { set4(nk, j, pack_nb(s0, k)); continue; }
+      int m = -1;
+      for (int l = 0; l <= D; l++) if (get4(v0, l) == w) m = l;
+      // in ghost m, the facet opposite the vertex ghost k lacks (v0[k])
+      int vk = get4(v0, k), f = -1;
+      for (int l = 0; l <= D; l++) if (get4(g[m], l) == vk) f = l;
+      set4(nk, j, pack_nb(s0 + 1 + m, f));
+    }
+    T.tn[s0 + 1 + k] = nk;
+  }
+  for (int k = 0; k <= D; k++) { T.state[pick[k]] = 1; T.loc[pick[k]] = s0; }
+  T.tcount[i] = base + D + 2;
+  inst_status[i] = 0;
+}
+
+// Initial conflict simplex of every other point: a ghost whose hull facet it
+// lies strictly beyond, else the initial simplex (it lies in it, closed).
+template <int D>
+__global__ void k_locate_init(TriView<D> T, int64_t npts, const int* toff, const int* inst_status,
+                              int* act, int* nact) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool active = false;
+  if (p < npts) {
+    int i = T.pinst[p];
+    if (inst_status[i] == 0 && T.state[p] == 0) {
+      active = true;
+      int s0 = toff[i];
+      int4 vv = T.tv[s0];
+      int loc = s0;
+      for (int j = 0; j <= D; j++) {
+        int4 t = vv;
+        set4(t, j, (int)p);
+        if (orient_tuple(T, t) < 0) { loc = nb_simplex(get4(T.tn[s0], j)); break; }
+      }
+      T.loc[p] = loc;
+    }
+  }
+  warp_append(act, nact, active, (int)p);
+}
+
+// ---------------------------------------------------------------- rounds
+template <int D>
+__global__ void k_pick(TriView<D> T, const int* act, int nact, unsigned round) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nact) return;
+  int p = act[idx];
+  atomicMax(&T.claimA[T.loc[p]], mkkey(round, p));
+}
+
+enum { CAND_OK = 0, CAND_LOST = 1, CAND_OVER = 2 };
+
+template <int D>
+__global__ void __launch_bounds__(128) k_cavity(TriView<D> T, const int* act, int nact, unsigned round,
+                                                CandScratch S) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nact) return;
+  int p = act[idx];
+  unsigned long long key = mkkey(round, p);
+  int t0 = T.loc[p];
+  if (*((volatile unsigned long long*)&T.claimA[t0]) != key) return;   // not its simplex's nominee
+  int slot = atomicAdd(S.count, 1);
+  if (slot >= S.cap) return;
+  S.cand[slot] = p;
+  int* C = S.cav + (int64_t)slot * S.capC;
+  int* B = S.bnd + (int64_t)slot * S.capB;
+  int nc = 0, nbd = 0, status = CAND_OK;
+  unsigned long long o = atomicMax(&T.claimC[t0], key);
+  if (o > key) status = CAND_LOST;
+  C[nc++] = t0;
+  for (int h = 0; h < nc && status == CAND_OK; h++) {
+    int t = C[h];
+    int4 nn = T.tn[t];
+    for (int i = 0; i <= D; i++) {
+      int u = nb_simplex(get4(nn, i));
+      if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 10); status = CAND_LOST; break; }
+      unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
+      if (cC == key) continue;                       // already in this region
+      if (cC > key) { status = CAND_LOST; break; }   // inside a stronger region
+      unsigned long long cA = *((volatile unsigned long long*)&T.claimA[u]);
+      bool conf = false;
+      if (cA != key) {                               // cA == key: known ring simplex
+        int4 vv = T.tv[u];
+        if (!verts_ok(T, vv)) { set_error(T.st, DT_E_INTERNAL, 11); status = CAND_LOST; break; }
+        int vt[4] = {vv.x, vv.y, vv.z, vv.w};
+        conf = in_conflict(T.pts, T.gid, vt, p);
+      }
+      if (conf) {
+        o = atomicMax(&T.claimC[u], key);
+        if (o > key) { status = CAND_LOST; break; }
+        o = atomicMax(&T.claimA[u], key);
+        if (o > key) { status = CAND_LOST; break; }
+        if (nc >= S.capC) { status = CAND_OVER; break; }
+        C[nc++] = u;
+      } else {
+        if (cA != key) atomicMax(&T.claimA[u], key);
+        if (nbd >= S.capB) { status = CAND_OVER; break; }
+        B[nbd++] = pack_nb(t, i);
+      }
+    }
+  }
+  if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
+  S.meta[slot] = make_int4(nc, nbd, status, 0);
+}
+
+// Winners replace their region by new simplices in fresh slots.
+template <int D>
+__global__ void __launch_bounds__(128) k_insert(TriView<D> T, unsigned round, CandScratch S) {
+  int total = min(*S.count, S.cap);
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < total; slot += gridDim.x * blockDim.x) {
+    int4 m = S.meta[slot];
+    if (m.z != CAND_OK) continue;
+    int p = S.cand[slot];
+    unsigned long long key = mkkey(round, p);
+    const int* C = S.cav + (int64_t)slot * S.capC;
+    const int* B = S.bnd + (int64_t)slot * S.capB;
+    int* OUT = S.outer + (int64_t)slot * S.capB;
+    int nc = m.x, nbd = m.y;
+    bool win = true;
+    for (int h = 0; h < nc && win; h++)
+      if (*((volatile unsigned long long*)&T.claimA[C[h]]) != key) win = false;
+    for (int b = 0; b < nbd && win; b++) {
+      int t = nb_simplex(B[b]), i = nb_face(B[b]);
+      int u = nb_simplex(*comp_ptr(T.tn, t, i));
+      if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 12); win = false; break; }
+      if (*((volatile unsigned long long*)&T.claimC[u]) > key) win = false;
+    }
+    if (!win) continue;
+    int inst = T.pinst[p];
+    int base = atomicAdd(&T.tcount[inst], nbd);
+    if (base + nbd > T.tend[inst]) { set_error(T.st, DT_E_OVERFLOW, 1); continue; }
+    // phase 1: remember the outside links, tag boundary facets with their new simplex
+    for (int b = 0; b < nbd; b++) {
+      int t = nb_simplex(B[b]), i = nb_face(B[b]);
+      int* cp = comp_ptr(T.tn, t, i);
+      OUT[b] = *cp;
+      *cp = TAGBIT | (base + b);
+    }
+    // phase 2: build the star of p over the boundary
+    for (int b = 0; b < nbd; b++) {
+      int t = nb_simplex(B[b]), i = nb_face(B[b]);
+      int4 vv = T.tv[t];
+      set4(vv, i, p);
+      int4 nn = make_int4(0, 0, 0, 0);
+      int out = OUT[b];
+      set4(nn, i, out);
+      if (slot_ok(T, nb_simplex(out))) *comp_ptr(T.tn, nb_simplex(out), nb_face(out)) = pack_nb(base + b, i);
+      else set_error(T.st, DT_E_INTERNAL, 13);
+      for (int j = 0; j <= D; j++) {
+        if (j == i) continue;
+        // rotate around the ridge (t minus slots i and j) inside the region
+        int cur = t, as = j, bs = i;
+        int link = -1;
+        for (int it = 0; it <= nc + 1; it++) {
+          int nx = *comp_ptr(T.tn, cur, as);
+          if (nx < 0) { link = pack_nb(nx & ~TAGBIT, bs); break; }
+          int nxt = nb_simplex(nx);
+          if (!slot_ok(T, nxt)) break;
+          int bvtx = get4(T.tv[cur], bs);
+          int4 nv = T.tv[nxt];
+          int nas = -1;
+          for (int l = 0; l <= D; l++) if (get4(nv, l) == bvtx) nas = l;
+          bs = nb_face(nx);
+          as = nas;
+          cur = nxt;
+          if (as < 0) break;
+        }
+        if (link < 0) { set_error(T.st, DT_E_INTERNAL, 2); link = 0; }
+        set4(nn, j, link);
+      }
+      T.tv[base + b] = vv;
+      T.tn[base + b] = nn;
+    }
+    // phase 3: retire the region; dead slots redirect to the first new simplex
+    for (int h = 0; h < nc; h++) {
+      int t = C[h];
+      *comp_ptr(T.tv, t, 0) = DEAD;
+      *comp_ptr(T.tn, t, 0) = pack_nb(base, 0);
+    }
+    T.state[p] = 1;
+    T.loc[p] = base;
+  }
+}
+
+// Visibility walk to a simplex in conflict with point p: a finite simplex
+// containing p (closed), or a ghost entered through its hull facet.
+template <int D>
+__device__ int walk_to(const TriView<D>& T, int s, int p, int limit) {
+  if (!slot_ok(T, s)) return -1;
+  int4 vv = T.tv[s];
+  for (int i = 0; i <= D; i++)
+    if (get4(vv, i) == INF_V) {
+      s = nb_simplex(get4(T.tn[s], i));
+      if (!slot_ok(T, s)) return -1;
+      vv = T.tv[s];
+      break;
+    }
+  int skip = -1;
+  for (int it = 0; it < limit; it++) {
+    bool ghost = false;
+    for (int i = 0; i <= D; i++) ghost |= (get4(vv, i) == INF_V);
+    if (ghost) return s;
+    if (!verts_ok(T, vv)) return -1;
+    int next = -1, nf = -1;
+    for (int i = 0; i <= D; i++) {
+      if (i == skip) continue;
+      int4 t = vv;
+      set4(t, i, p);
+      if (orient_tuple(T, t) < 0) {
+        int nx = get4(T.tn[s], i);
+        next = nb_simplex(nx);
+        nf = nb_face(nx);
+        break;
+      }
+    }
+    if (next < 0) return s;
+    if (!slot_ok(T, next)) return -1;
+    s = next;
+    skip = nf;
+    vv = T.tv[s];
+  }
+  return -1;
+}
+
+template <int D>
+__global__ void k_relocate(TriView<D> T, const int* act, int nact, int* act_out, int* nact_out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  bool keep = false;
+  int p = -1;
+  if (idx < nact) {
+    p = act[idx];
+    if (T.state[p] == 0) {
+      keep = true;
+      int s = T.loc[p];
+      int4 vv = T.tv[s];
+      if (vv.x == DEAD) {
+        s = nb_simplex(T.tn[s].x);
+        int r = walk_to(T, s, p, 1 << 22);
+        if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); r = 0; keep = false; }
+        T.loc[p] = r;
+      }
+    }
+  }
+  warp_append(act_out, nact_out, keep, p);
+}
+
+// ---------------------------------------------------------------- host
+static __global__ void k_read_pred_counters(unsigned long long* calls, int* range, int reset) {
+  *calls = g_exact_calls;
+  *range = g_range_error;
+  if (reset) { g_exact_calls = 0; g_range_error = 0; }
+}
+
+int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool reset) {
+  void* buf = pool_get(c, "predctr_eng", 64);
+  if (!buf) return set_err(c, DT_E_NOMEM, "predicate counters");
+  k_read_pred_counters<<<1, 1, 0, c->stream>>>((unsigned long long*)buf, (int*)((char*)buf + 8), reset);
+  unsigned long long h[2];
+  CUDA_OK(cudaMemcpyAsync(h, buf, 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaStreamSynchronize(c->stream));
+  *calls = h[0];
+  *range = (int)(h[1] & 0xffffffff);
+  return 0;
+}
+
+template <int D>
+static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* gid, const int* pinst,
+                        int64_t npts, const std::vector<int64_t>& poff, const std::string& tag) {
+  using P = typename PT<D>::T;
+  cudaStream_t s = c->stream;
+  int ninst = (int)poff.size() - 1;
+  run.dim = D;
+  run.ninst = ninst;
+  run.npts = npts;
+  run.h_poff = poff;
+  run.rounds = 0;
+  // arena: per instance mult * n_i + pad slots
+  const int64_t mult = D == 2 ? 8 : 36, pad = 32;
+  int64_t grow = 1;
+  for (int attempt = 0; attempt < 4; attempt++) {
+    run.h_toff.assign(ninst + 1, 0);
+    for (int i = 0; i < ninst; i++)
+      run.h_toff[i + 1] = run.h_toff[i] + grow * (mult * (poff[i + 1] - poff[i]) + pad);
+    int64_t total = run.h_toff[ninst];
+    if (total >= (int64_t(1) << 29)) return set_err(c, DT_E_NOMEM, "simplex arena exceeds 2^29 slots");
+    run.total_slots = total;
+    run.tv = pool_get(c, tag + ".tv", sizeof(int4) * total);
+    run.tn = pool_get(c, tag + ".tn", sizeof(int4) * total);
+    auto* claimA = (unsigned long long*)pool_get(c, tag + ".cA", 8 * total);
+    auto* claimC = (unsigned long long*)pool_get(c, tag + ".cC", 8 * total);
+    run.tcount = (int*)pool_get(c, tag + ".tcount", 4 * (ninst + 1));
+    run.toff = (int*)pool_get(c, tag + ".toff", 4 * (ninst + 1));
+    run.tend = (int*)pool_get(c, tag + ".tend", 4 * (ninst + 1));
+    run.inst_status = (int*)pool_get(c, tag + ".ist", 4 * (ninst + 1));
+    long long* dpoff = (long long*)pool_get(c, tag + ".poff", 8 * (ninst + 1));
+    int* loc = (int*)pool_get(c, tag + ".loc", 4 * std::max<int64_t>(npts, 1));
+    unsigned char* state = (unsigned char*)pool_get(c, tag + ".state", std::max<int64_t>(npts, 1));
+    int* act0 = (int*)pool_get(c, "eng.act0", 4 * std::max<int64_t>(npts, 1));
+    int* act1 = (int*)pool_get(c, "eng.act1", 4 * std::max<int64_t>(npts, 1));
+    int* cnt = (int*)pool_get(c, "eng.cnt", 64);
+    if (!run.tv || !run.tn || !claimA || !claimC || !run.tcount || !run.toff || !run.tend ||
+        !run.inst_status || !dpoff || !loc || !state || !act0 || !act1 || !cnt)
+      return set_err(c, DT_E_NOMEM, "engine buffers");
+    std::vector<int> h_toff32(ninst + 1), h_tend(ninst + 1);
+    for (int i = 0; i <= ninst; i++) h_toff32[i] = (int)run.h_toff[i];
+    for (int i = 0; i < ninst; i++) h_tend[i] = (int)run.h_toff[i + 1];
+    std::vector<long long> h_poff(poff.begin(), poff.end());
+    CUDA_OK(cudaMemcpyAsync(run.toff, h_toff32.data(), 4 * (ninst + 1), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemcpyAsync(run.tend, h_tend.data(), 4 * (ninst + 1), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemcpyAsync(dpoff, h_poff.data(), 8 * (ninst + 1), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemsetAsync(claimA, 0, 8 * total, s));
+    CUDA_OK(cudaMemsetAsync(claimC, 0, 8 * total, s));
+    CUDA_OK(cudaMemsetAsync(state, 0, std::max<int64_t>(npts, 1), s));
+    CUDA_OK(cudaMemsetAsync(cnt, 0, 64, s));
+    CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+
+    TriView<D> T;
+    T.pts = (const P*)pts;
+    T.gid = gid;
+    T.pinst = pinst;
+    T.tv = (int4*)run.tv;
+    T.tn = (int4*)run.tn;
+    T.claimA = claimA;
+    T.claimC = claimC;
+    T.tcount = run.tcount;
+    T.tend = run.tend;
+    T.loc = loc;
+    T.state = state;
+    T.st = c->status;
+    T.nslots = (int)total;
+    T.npts = (int)npts;
+
+    k_init<D><<<ceil_div(ninst, 64), 64, 0, s>>>(T, ninst, dpoff, run.toff, run.inst_status);
+    if (npts > 0)
+      k_locate_init<D><<<(unsigned)ceil_div<int64_t>(npts, 256), 256, 0, s>>>(T, npts, run.toff,
+                                                                             run.inst_status, act0, cnt);
+    int* h = c->counters_host;
+    CUDA_OK(cudaMemcpyAsync(h, cnt, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    int nact = h[0];
+    // candidate scratch
+    int capC = D == 2 ? 32 : 96, capB = D == 2 ? 48 : 192;
+    if (c->cfg.cavity_cap > 0) {
+      capC = c->cfg.cavity_cap;
+      capB = D == 2 ? c->cfg.cavity_cap * 3 / 2 : c->cfg.cavity_cap * 2;
+    }
+    int overflow_grow = 0;
+    bool failed = false;
+    int* ain = act0;
+    int* aout = act1;
+    unsigned round = 0;
+    while (nact > 0) {
+      round++;
+      if (round > 200000) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
+      int capCand = (int)std::min<int64_t>(nact, int64_t(1) << 22);
+      CandScratch S;
+      S.cap = capCand;
+      S.capC = capC << overflow_grow;
+      S.capB = capB << overflow_grow;
+      S.cand = (int*)pool_get(c, "eng.cand", 4 * (size_t)capCand);
+      S.meta = (int4*)pool_get(c, "eng.meta", 16 * (size_t)capCand);
+      S.cav = (int*)pool_get(c, "eng.cav", 4 * (size_t)capCand * S.capC);
+      S.bnd = (int*)pool_get(c, "eng.bnd", 4 * (size_t)capCand * S.capB);
+      S.outer = (int*)pool_get(c, "eng.outer", 4 * (size_t)capCand * S.capB);
+      S.count = cnt + 4;
+      if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
+      CUDA_OK(cudaMemsetAsync(cnt + 4, 0, 8, s));
+      unsigned nb = (unsigned)ceil_div(nact, 256);
+      k_pick<D><<<nb, 256, 0, s>>>(T, ain, nact, round);
+      k_cavity<D><<<(unsigned)ceil_div(nact, 128), 128, 0, s>>>(T, ain, nact, round, S);
+      unsigned ib = (unsigned)std::min<int64_t>(ceil_div<int64_t>(capCand, 128), 152 * 16);
+      k_insert<D><<<ib, 128, 0, s>>>(T, round, S);
+      k_relocate<D><<<nb, 256, 0, s>>>(T, ain, nact, aout, cnt + 5);
+      CUDA_OK(cudaMemcpyAsync(h, cnt + 5, 4, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { failed = true; break; }
+      if (c->status_host->error) return check_status(c, "insertion round");
+      int nnew = h[0];
+      if (nnew == nact) {
+        // no insertion anywhere: only possible when candidates overflowed their scratch
+        if (c->status_host->overflow_cav && overflow_grow < 8) {
+          overflow_grow++;
+          CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));
+        } else {
+          return set_err(c, DT_E_INTERNAL, "insertion round made no progress");
+        }
+      }
+      nact = nnew;
+      std::swap(ain, aout);
+    }
+    run.rounds = (int)round;
+    if (failed) { grow *= 2; continue; }
+    run.h_status.assign(ninst, 0);
+    run.h_tcount.assign(ninst, 0);
+    CUDA_OK(cudaMemcpyAsync(run.h_status.data(), run.inst_status, 4 * ninst, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(run.h_tcount.data(), run.tcount, 4 * ninst, cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    unsigned long long calls; int range;
+    int rc = pred_counters_engine(c, &calls, &range, false);
+    if (rc) return rc;
+    if (range) return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
+    return 0;
+  }
+  return set_err(c, DT_E_OVERFLOW, "simplex arena overflow after retries");
+}
+
+int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,
+               int64_t npts, const std::vector<int64_t>& poff, const std::string& tag) {
+  if (dim == 2) return engine_run_t<2>(c, run, pts, gid, pinst, npts, poff, tag);
+  return engine_run_t<3>(c, run, pts, gid, pinst, npts, poff, tag);
+}
+
+}  // namespace gdt

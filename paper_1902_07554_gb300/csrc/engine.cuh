@@ -1,0 +1,81 @@
+// engine.cuh -- batched parallel Delaunay insertion on the GPU.
+//
+// Triangulates many independent point sets ("instances": the k partitions of
+// Alg. 1, the sample of Alg. 2, the border vertex set, or a batch of separate
+// problems) in the same kernel launches.  Each instance is built by
+// Bowyer-Watson insertion with an explicit infinite vertex; points are
+// inserted in rounds:
+//   pick    -- every simplex holding uninserted points nominates the one with
+//              the highest priority (one atomicMax per point);
+//   cavity  -- each nominee grows its conflict region (simplices whose
+//              perturbed circumsphere contains it) and claims it, plus the ring
+//              of simplices across the region's boundary, with 64-bit
+//              (round, priority) keys;
+//   insert  -- a nominee whose region and ring are not touched by a stronger
+//              nominee's region (and whose region is not inside a stronger
+//              nominee's ring) replaces its region by the star of new simplices
+//              over the boundary facets.  Such insertions commute, so the
+//              round's result equals inserting the winners one at a time;
+//   relocate-- points whose conflict simplex was destroyed walk (visibility
+//              walk with exact orientation) to a simplex in conflict with them.
+// The strongest nominee of an instance always wins, so every round inserts at
+// least one point per unfinished instance.
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+#include "predicates.cuh"
+
+namespace gdt {
+
+// Device views of one engine run.
+template <int D>
+struct TriView {
+  using P = typename PT<D>::T;
+  const P* pts;             // points (all instances, concatenated)
+  const int* gid;           // global index of each point (perturbation rank)
+  const int* pinst;         // instance of each point
+  int4* tv;                 // simplex vertex tuples (D+1 used)
+  int4* tn;                 // packed neighbour links
+  unsigned long long* claimA;   // strongest key having the simplex in region or ring
+  unsigned long long* claimC;   // strongest key having the simplex in its region
+  int* tcount;              // per instance: next free simplex slot (absolute)
+  const int* tend;          // per instance: end of its simplex arena (absolute)
+  int* loc;                 // per point: a simplex in conflict with it (or -1)
+  unsigned char* state;     // per point: 0 uninserted, 1 inserted
+  DevStatus* st;
+  int nslots;               // total simplex slots (bounds for every link)
+  int npts;                 // total points (bounds for every vertex)
+};
+
+struct CandScratch {
+  int* cand;      // candidate point per slot
+  int4* meta;     // (cavity size, boundary size, status, 0)
+  int* cav;       // capC entries per slot
+  int* bnd;       // capB entries per slot (packed simplex, facet)
+  int* outer;     // capB entries per slot
+  int* count;     // slots taken this round
+  int cap, capC, capB;
+};
+
+// Host-side engine run: owns the buffers of one triangulation batch.
+struct EngineRun {
+  int dim = 0;
+  int ninst = 0;
+  int64_t npts = 0;
+  int64_t total_slots = 0;
+  std::vector<int64_t> h_poff;   // instance point offsets (host)
+  std::vector<int64_t> h_toff;   // instance simplex arena offsets (host)
+  std::vector<int> h_status;     // per instance: 0 ok, 1 degenerate, 2 too small
+  std::vector<int> h_tcount;     // per instance: slots used (absolute end)
+  int rounds = 0;
+  // device buffers (owned by the context's allocator)
+  void* tv = nullptr;
+  void* tn = nullptr;
+  int* tcount = nullptr;
+  int* toff = nullptr;
+  int* tend = nullptr;
+  int* inst_status = nullptr;
+};
+
+}  // namespace gdt

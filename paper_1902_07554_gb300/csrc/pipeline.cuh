@@ -1,0 +1,13 @@
+// pipeline.cuh -- orchestration of Alg. 1 (divide, partial DTs, border,
+// border DT, merge) on the context's stream.
+#pragma once
+#include "ctx.cuh"
+
+namespace gdt {
+int run_pipeline(dt_ctx* c, const double* points, int64_t n, int dim, int k, double frac);
+int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out);
+void* stage_in(dt_ctx* c, const void* src, size_t bytes, const std::string& name, int* rc);
+int copy_out(dt_ctx* c, void* dst, const void* src, size_t bytes);
+bool is_device_ptr(const void* p);
+__global__ void k_iota(int* a, int64_t n, int start);
+}  // namespace gdt

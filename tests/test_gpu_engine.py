@@ -1,0 +1,111 @@
+"""GPU parity: device predicates and the direct (k = 1) triangulation against
+the CPU oracle, element by element (integer output: bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+import pointsets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tri():
+    from paper_1902_07554_gb300 import Triangulator
+    t = Triangulator(0)
+    yield t
+    t.close()
+
+
+def _tuples(rng, n, w, m):
+    return np.array([rng.choice(n, w, replace=False) for _ in range(m)], dtype=np.int32)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_predicates_random(tri, D):
+    rng = np.random.default_rng(1 + D)
+    P = rng.random((200, D))
+    for kind, w in [("orient", D + 1), ("insphere_raw", D + 2), ("insphere", D + 2), ("closer", 3)]:
+        T = _tuples(rng, 200, w, 2000)
+        assert np.array_equal(tri.eval_predicates(P, kind, T), oracle.predicates(P, kind, T)), kind
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_predicates_degenerate_and_near_degenerate(tri, D):
+    rng = np.random.default_rng(7)
+    base = pointsets.grid((4,) * D) * 0.1 + 0.3
+    gid = rng.permutation(len(base)).astype(np.int64)
+    for trial in range(4):
+        P = base.copy()
+        if trial:
+            idx = rng.choice(len(P), 5, replace=False)
+            for i in idx:
+                c = rng.integers(D)
+                P[i, c] = np.nextafter(P[i, c], np.inf if rng.random() < 0.5 else -np.inf)
+        for kind, w in [("orient", D + 1), ("insphere_raw", D + 2), ("insphere", D + 2), ("closer", 3)]:
+            T = _tuples(rng, len(P), w, 3000)
+            assert np.array_equal(tri.eval_predicates(P, kind, T, gid), oracle.predicates(P, kind, T, gid)), kind
+    assert tri.stats().exact_calls > 0
+
+
+def test_predicates_wide_exponent_range(tri):
+    P = np.array([[1e-200, 0.0], [1.0, 1e-150], [0.0, 1.0], [1.0, 1.0], [1e100, 1e-100], [3e-5, 7e-9]])
+    rng = np.random.default_rng(0)
+    for kind, w in [("orient", 3), ("insphere_raw", 4), ("closer", 3)]:
+        T = _tuples(rng, 6, w, 300)
+        try:
+            got = tri.eval_predicates(P, kind, T)
+        except Exception as e:            # the exact path may report DT_E_RANGE; never a wrong sign
+            assert "RANGE" in str(e)
+            continue
+        assert np.array_equal(got, oracle.predicates(P, kind, T)), kind
+
+
+@pytest.mark.parametrize("D,n,kind", [(2, 10, "uniform"), (2, 1000, "uniform"), (2, 20000, "normal"),
+                                      (3, 12, "uniform"), (3, 1000, "uniform"), (3, 20000, "clustered")])
+def test_direct_dt_matches_oracle(tri, D, n, kind):
+    if kind == "uniform":
+        P = pointsets.uniform(n, D, 5)
+    elif kind == "normal":
+        P = pointsets.normal(n, D, 5)
+    else:
+        P = pointsets.clustered(n, 5)
+    got = tri.triangulate(P, k=1)
+    assert got.dtype == np.int32
+    assert np.array_equal(got.astype(np.int64), oracle.delaunay(P))
+    assert tri.stats().simplices == len(got)
+
+
+@pytest.mark.parametrize("shape", [(7, 5), (12, 12), (4, 4, 4), (5, 3, 2), (6, 6, 6)])
+def test_direct_dt_degenerate_grids(tri, shape):
+    P = pointsets.grid(shape, seed=3)
+    got = tri.triangulate(P, k=1)
+    assert np.array_equal(got.astype(np.int64), oracle.delaunay(P))
+
+
+def test_direct_dt_cocircular(tri):
+    P = pointsets.cocircular(20, 2)
+    got = tri.triangulate(P, k=1)
+    assert np.array_equal(got.astype(np.int64), oracle.delaunay(P))
+
+
+def test_errors(tri):
+    from paper_1902_07554_gb300 import DTError
+    P = pointsets.uniform(100, 2, 1)
+    P[10] = P[20]
+    with pytest.raises(DTError, match="DUPLICATE"):
+        tri.triangulate(P)
+    L = np.stack([np.arange(50.0), 3 * np.arange(50.0)], axis=1)
+    with pytest.raises(DTError, match="DEGENERATE"):
+        tri.triangulate(L)
+    Q = pointsets.uniform(50, 3, 2)
+    Q[:, 2] = 0.5
+    with pytest.raises(DTError, match="DEGENERATE"):
+        tri.triangulate(Q)
+    bad = pointsets.uniform(10, 2, 1)
+    bad[3, 1] = np.nan
+    with pytest.raises(DTError, match="ARG"):
+        tri.triangulate(bad)
+    # the context stays usable after errors
+    P = pointsets.uniform(500, 2, 9)
+    assert np.array_equal(tri.triangulate(P).astype(np.int64), oracle.delaunay(P))
