@@ -31,13 +31,14 @@ __device__ __forceinline__ int inst_of_slot(const int* toff, int ninst, int s) {
 // mapped to global indices and sorted; keep (optional, per slot) filters.
 template <int D>
 __global__ void k_collect_finite(const int4* tv, const int* toff, const int* tcount, int ninst, int nslots,
-                                 const int* gid, const unsigned char* drop, int4* rows, int* nrows) {
+                                 const int* gid, const unsigned char* flag, int mode, int4* rows, int* nrows) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   bool take = false;
   int4 r = make_int4(0, 0, 0, 0);
   if (s < nslots) {
     int i = inst_of_slot(toff, ninst, s);
-    if (s < tcount[i] && !(drop && drop[s])) {
+    bool sel = mode == 0 || (mode == 1 && !flag[s]) || (mode == 2 && flag[s]);
+    if (s < tcount[i] && sel) {
       int4 v = tv[s];
       bool fin = v.x >= 0 && v.y >= 0 && v.z >= 0 && (D == 2 || v.w >= 0);
       if (fin) {
@@ -121,10 +122,11 @@ int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64
   return 0;
 }
 
-// Collect the finite live simplices of an engine run (optionally dropping
-// flagged slots) as canonical rows in *rows (pool-owned), count in *nrows.
-int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsigned char* drop, int4** rows,
-                   int64_t* nrows, const std::string& tag) {
+// Collect the finite live simplices of an engine run as canonical rows in
+// *rows (pool-owned), count in *nrows.  mode 0: all; 1: slots not flagged;
+// 2: flagged slots only.
+int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsigned char* flag, int mode,
+                   int4** rows, int64_t* nrows, const std::string& tag) {
   cudaStream_t s = c->stream;
   int64_t ns = run.total_slots;
   int4* r = (int4*)pool_get(c, tag + ".rows", 16 * std::max<int64_t>(ns / 4, 16));
@@ -137,12 +139,13 @@ int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsign
   r = (int4*)pool_get(c, tag + ".rows", 16 * std::max<int64_t>(used, 16));
   if (!r) return set_err(c, DT_E_NOMEM, "collect rows");
   unsigned g = (unsigned)ceil_div<int64_t>(ns, 256);
+  if (mode && !flag) mode = 0;
   if (run.dim == 2)
     k_collect_finite<2><<<g, 256, 0, s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
-                                          drop, r, cnt);
+                                          flag, mode, r, cnt);
   else
     k_collect_finite<3><<<g, 256, 0, s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
-                                          drop, r, cnt);
+                                          flag, mode, r, cnt);
   int h = 0;
   CUDA_OK(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));

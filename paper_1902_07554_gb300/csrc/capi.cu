@@ -12,8 +12,7 @@ using namespace gdt;
 
 namespace gdt {
 const char* last_cuda_fail();
-int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsigned char* drop, int4** rows,
-                   int64_t* nrows, const std::string& tag);
+
 int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool reset);
 }  // namespace gdt
 
@@ -127,7 +126,7 @@ int copy_out(dt_ctx* c, void* dst, const void* src, size_t bytes) {
   return 0;
 }
 
-// Row-major (n x D) doubles -> the engine's point layout (double2 / double4),
+// Row-major (n x D) doubles -> the engine's point layout (double2 / double4_32a),
 // with a finiteness check.
 template <int D>
 __global__ void k_pack_points(const double* in, int64_t n, typename PT<D>::T* out, int* bad) {
@@ -137,7 +136,7 @@ __global__ void k_pack_points(const double* in, int64_t n, typename PT<D>::T* ou
   if (!isfinite(x) || !isfinite(y) || !isfinite(z) || fabs(x) > 1e300 || fabs(y) > 1e300 || fabs(z) > 1e300)
     atomicExch(bad, 1);
   if constexpr (D == 2) out[i] = make_double2(x, y);
-  else out[i] = make_double4(x, y, z, 0.0);
+  else out[i] = make_double4_32a(x, y, z, 0.0);
 }
 
 __global__ void k_iota(int* a, int64_t n, int start) {
@@ -164,13 +163,14 @@ __global__ void k_dup_check(const typename PT<D>::T* P, int64_t n, int* table, u
   atomicExch(dup, 2);
 }
 
-int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out) {
+int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out, const char* tag) {
   int rc = 0;
-  const double* src = (const double*)stage_in(c, points, sizeof(double) * n * dim, "in.raw", &rc);
+  std::string t(tag);
+  const double* src = (const double*)stage_in(c, points, sizeof(double) * n * dim, t + ".raw", &rc);
   if (rc) return rc;
-  size_t psz = dim == 2 ? sizeof(double2) : sizeof(double4);
-  void* P = pool_get(c, "in.pts", psz * n);
-  int* flags = (int*)pool_get(c, "in.flags", 16);
+  size_t psz = dim == 2 ? sizeof(double2) : sizeof(double4_32a);
+  void* P = pool_get(c, t + ".pts", psz * n);
+  int* flags = (int*)pool_get(c, t + ".flags", 16);
   unsigned tsize = 1;
   while (tsize < 2 * n) tsize <<= 1;
   int* table = (int*)pool_get(c, "in.dup", 4 * (size_t)tsize);
@@ -182,8 +182,8 @@ int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_o
     k_pack_points<2><<<g, 256, 0, c->stream>>>(src, n, (double2*)P, flags);
     k_dup_check<2><<<g, 256, 0, c->stream>>>((const double2*)P, n, table, tsize - 1, flags + 1);
   } else {
-    k_pack_points<3><<<g, 256, 0, c->stream>>>(src, n, (double4*)P, flags);
-    k_dup_check<3><<<g, 256, 0, c->stream>>>((const double4*)P, n, table, tsize - 1, flags + 1);
+    k_pack_points<3><<<g, 256, 0, c->stream>>>(src, n, (double4_32a*)P, flags);
+    k_dup_check<3><<<g, 256, 0, c->stream>>>((const double4_32a*)P, n, table, tsize - 1, flags + 1);
   }
   int h[2];
   CUDA_OK(cudaMemcpyAsync(h, flags, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -334,7 +334,7 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
   int rc = 0;
   const double* src = (const double*)stage_in(c, points, sizeof(double) * n * dim, "pred.raw", &rc);
   if (rc) return rc;
-  size_t psz = dim == 2 ? sizeof(double2) : sizeof(double4);
+  size_t psz = dim == 2 ? sizeof(double2) : sizeof(double4_32a);
   void* P = pool_get(c, "pred.pts", psz * n);
   int* g32 = (int*)pool_get(c, "pred.gid", 4 * n);
   int* flags = (int*)pool_get(c, "pred.flags", 16);
@@ -357,8 +357,8 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
     k_pack_points<2><<<g, 256, 0, c->stream>>>(src, n, (double2*)P, flags);
     k_eval_pred<2><<<gm, 128, 0, c->stream>>>((const double2*)P, g32, kind, tup, m, (int)n, o, flags + 1);
   } else {
-    k_pack_points<3><<<g, 256, 0, c->stream>>>(src, n, (double4*)P, flags);
-    k_eval_pred<3><<<gm, 128, 0, c->stream>>>((const double4*)P, g32, kind, tup, m, (int)n, o, flags + 1);
+    k_pack_points<3><<<g, 256, 0, c->stream>>>(src, n, (double4_32a*)P, flags);
+    k_eval_pred<3><<<gm, 128, 0, c->stream>>>((const double4_32a*)P, g32, kind, tup, m, (int)n, o, flags + 1);
   }
   unsigned long long* ctr = (unsigned long long*)pool_get(c, "pred.ctr", 32);
   if (!ctr) return set_err(c, DT_E_NOMEM, "predicate counters");

@@ -63,5 +63,7 @@ int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* g
 // keep (optional, per slot) filters simplices.
 int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64_t nbuckets,
                       int32_t** out, int64_t* nout, const std::string& tag);
+int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsigned char* flag, int mode,
+                   int4** rows, int64_t* nrows, const std::string& tag);
 
 }  // namespace gdt

@@ -107,7 +107,7 @@ __global__ void k_gather_pts(const typename PT<D>::T* P, const int* ids, int64_t
 int gather_points(dt_ctx* c, int dim, const void* P, const int* ids, int64_t m, void* out) {
   unsigned g = (unsigned)ceil_div<int64_t>(std::max<int64_t>(m, 1), 256);
   if (dim == 2) k_gather_pts<2><<<g, 256, 0, c->stream>>>((const double2*)P, ids, m, (double2*)out);
-  else k_gather_pts<3><<<g, 256, 0, c->stream>>>((const double4*)P, ids, m, (double4*)out);
+  else k_gather_pts<3><<<g, 256, 0, c->stream>>>((const double4_32a*)P, ids, m, (double4_32a*)out);
   return 0;
 }
 
@@ -229,6 +229,12 @@ __global__ void k_fill_csr(const int2* E, const long long* w, int64_t m, const i
   col[b] = e.x; cw[b] = w[i];
 }
 
+int graph_bbox(dt_ctx* c, int dim, const void* PS, int64_t eta, double* box) {
+  if (dim == 2) k_bbox<2><<<1, 256, 0, c->stream>>>((const double2*)PS, eta, box);
+  else k_bbox<3><<<1, 256, 0, c->stream>>>((const double4_32a*)PS, eta, box);
+  return 0;
+}
+
 int build_csr(dt_ctx* c, SampleGraph& G) {
   cudaStream_t s = c->stream;
   int64_t eta = G.eta;
@@ -289,11 +295,11 @@ int sample_graph(dt_ctx* c, const EngineRun& run, const void* PS, int dim, int k
   if (!G.E || !G.w) return set_err(c, DT_E_NOMEM, "graph edges");
   k_write_unique<<<gu, 128, 0, s>>>(vout, ustart, ucount, upos, eta, G.E);
   if (dim == 2) k_bbox<2><<<1, 256, 0, s>>>((const double2*)PS, eta, G.box);
-  else k_bbox<3><<<1, 256, 0, s>>>((const double4*)PS, eta, G.box);
+  else k_bbox<3><<<1, 256, 0, s>>>((const double4_32a*)PS, eta, G.box);
   unsigned gm = (unsigned)ceil_div<int64_t>(std::max(m, 1), 256);
   if (m) {
     if (dim == 2) k_edge_weights<2><<<gm, 256, 0, s>>>((const double2*)PS, G.E, m, G.box, kind, G.w);
-    else k_edge_weights<3><<<gm, 256, 0, s>>>((const double4*)PS, G.E, m, G.box, kind, G.w);
+    else k_edge_weights<3><<<gm, 256, 0, s>>>((const double4_32a*)PS, G.E, m, G.box, kind, G.w);
   }
   return build_csr(c, G);
 }
@@ -411,7 +417,7 @@ int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, d
   int bits = dim == 2 ? 16 : 10;
   unsigned g = (unsigned)ceil_div<int64_t>(eta, 256);
   if (dim == 2) k_hilbert<2><<<g, 256, 0, s>>>((const double2*)PS, eta, G.box, bits, keys, idx);
-  else k_hilbert<3><<<g, 256, 0, s>>>((const double4*)PS, eta, G.box, bits, keys, idx);
+  else k_hilbert<3><<<g, 256, 0, s>>>((const double4_32a*)PS, eta, G.box, bits, keys, idx);
   int rc = radix_sort_pairs<uint32_t, int>(c, keys, idx, eta, bits * dim, "p.sort");
   if (rc) return rc;
   k_initial_blocks<<<g, 256, 0, s>>>(idx, eta, k, block);
@@ -532,7 +538,7 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
   double* box = (double*)pool_get(c, "lw.box", 48);
   if (!box) return set_err(c, DT_E_NOMEM, "label box");
   if (dim == 2) k_bbox<2><<<1, 256, 0, s>>>((const double2*)P, n, box);
-  else k_bbox<3><<<1, 256, 0, s>>>((const double4*)P, n, box);
+  else k_bbox<3><<<1, 256, 0, s>>>((const double4_32a*)P, n, box);
   double hb[6];
   CUDA_OK(cudaMemcpyAsync(hb, box, 48, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
@@ -557,7 +563,7 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
   unsigned gm = (unsigned)ceil_div<int64_t>(m, 256);
   k_fill_int<<<(unsigned)ceil_div<int64_t>(ncell, 256), 256, 0, s>>>(cv0, ncell, 0x7fffffff);
   if (dim == 2) k_seed_cells<2><<<gm, 256, 0, s>>>((const double2*)S, m, sg, cv0);
-  else k_seed_cells<3><<<gm, 256, 0, s>>>((const double4*)S, m, sg, cv0);
+  else k_seed_cells<3><<<gm, 256, 0, s>>>((const double4_32a*)S, m, sg, cv0);
   unsigned gc = (unsigned)ceil_div<int64_t>(ncell, 256);
   for (int pass = 0; pass < 6; pass++) {
     if (dim == 2) k_dilate<2><<<gc, 256, 0, s>>>(cv0, cv1, sg, ncell);
@@ -569,7 +575,7 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
     k_label_walk<2><<<gn, 128, 0, s>>>((const double2*)P, n, (const double2*)S, srank, G.rowptr, G.col, block, cv0, sg,
                                        m, label, nearest, c->status);
   else
-    k_label_walk<3><<<gn, 128, 0, s>>>((const double4*)P, n, (const double4*)S, srank, G.rowptr, G.col, block, cv0, sg,
+    k_label_walk<3><<<gn, 128, 0, s>>>((const double4_32a*)P, n, (const double4_32a*)S, srank, G.rowptr, G.col, block, cv0, sg,
                                        m, label, nearest, c->status);
   return 0;
 }
@@ -642,7 +648,7 @@ int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label) {
     CUDA_OK(cudaMemcpyAsync(tabs, hs.data(), 4 * 4 * (size_t)k, cudaMemcpyHostToDevice, s));
     int cdim = depth % dim;
     if (dim == 2) k_kd_keys<2><<<g, 256, 0, s>>>((const double2*)P, n, cdim, keys, idx);
-    else k_kd_keys<3><<<g, 256, 0, s>>>((const double4*)P, n, cdim, keys, idx);
+    else k_kd_keys<3><<<g, 256, 0, s>>>((const double4_32a*)P, n, cdim, keys, idx);
     int rc = radix_sort_pairs<unsigned long long, int>(c, keys, idx, n, 64, "kd.s1");
     if (rc) return rc;
     k_kd_nodekeys<<<g, 256, 0, s>>>(idx, label, n, nkeys);
@@ -690,7 +696,7 @@ int scatter_by_label(dt_ctx* c, int dim, const void* P, const int* label, int64_
   CUDA_OK(cudaMemcpyAsync(dpoff, hp.data(), 4 * (k + 1), cudaMemcpyHostToDevice, s));
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
   if (dim == 2) k_scatter<2><<<g, 256, 0, s>>>((const double2*)P, label, rank, dpoff, n, (double2*)Ps, gid, pinst, nullptr);
-  else k_scatter<3><<<g, 256, 0, s>>>((const double4*)P, label, rank, dpoff, n, (double4*)Ps, gid, pinst, nullptr);
+  else k_scatter<3><<<g, 256, 0, s>>>((const double4_32a*)P, label, rank, dpoff, n, (double4_32a*)Ps, gid, pinst, nullptr);
   return 0;
 }
 

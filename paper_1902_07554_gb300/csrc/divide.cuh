@@ -23,6 +23,7 @@ int select_sample(dt_ctx* c, int64_t n, int64_t eta, uint64_t seed, int* ids);
 int gather_points(dt_ctx* c, int dim, const void* P, const int* ids, int64_t m, void* out);
 int sample_graph(dt_ctx* c, const EngineRun& run, const void* PS, int dim, int kind, SampleGraph& G);
 int build_csr(dt_ctx* c, SampleGraph& G);
+int graph_bbox(dt_ctx* c, int dim, const void* PS, int64_t eta, double* box);
 void partition_bounds(int64_t eta, int k, double eps, int* lmin, int* lmax);
 int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, double eps, int rounds, int* block);
 int cut_weight(dt_ctx* c, const SampleGraph& G, const int* block, long long* out);

@@ -1,6 +1,7 @@
 // engine.cu -- batched parallel Bowyer-Watson insertion (see engine.cuh).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "ctx.cuh"
 
@@ -32,7 +33,7 @@ __device__ __forceinline__ void warp_append(int* list, int* counter, bool pred, 
   if (pred) list[base + __popc(mask & ((1u << lane) - 1))] = val;
 }
 
-__device__ __forceinline__ bool collinear3(double4 a, double4 b, double4 c) {
+__device__ __forceinline__ bool collinear3(double4_32a a, double4_32a b, double4_32a c) {
   double2 pa, pb, pc;
   pa = make_double2(a.x, a.y); pb = make_double2(b.x, b.y); pc = make_double2(c.x, c.y);
   if (orient2(pa, pb, pc) != 0) return false;
@@ -82,9 +83,9 @@ __global__ void k_init(TriView<D> T, int ninst, const long long* poff, const int
     if (np == 1) {
       ok = true;
     } else if (D == 3 && np == 2) {
-      ok = !collinear3(reinterpret_cast<const double4*>(T.pts)[pick[0]],
-                       reinterpret_cast<const double4*>(T.pts)[pick[1]],
-                       reinterpret_cast<const double4*>(T.pts)[q]);
+      ok = !collinear3(reinterpret_cast<const double4_32a*>(T.pts)[pick[0]],
+                       reinterpret_cast<const double4_32a*>(T.pts)[pick[1]],
+                       reinterpret_cast<const double4_32a*>(T.pts)[q]);
     } else {
       int t[4] = {pick[0], pick[1], pick[2], pick[3]};
       t[np] = (int)q;
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(128) k_insert(TriView<D> T, unsigned round, Ca
     }
     T.state[p] = 1;
     T.loc[p] = base;
+    atomicAdd(S.count + 2, 1);
   }
 }
 
@@ -479,7 +481,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       S.outer = (int*)pool_get(c, "eng.outer", 4 * (size_t)capCand * S.capB);
       S.count = cnt + 4;
       if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
-      CUDA_OK(cudaMemsetAsync(cnt + 4, 0, 8, s));
+      CUDA_OK(cudaMemsetAsync(cnt + 4, 0, 16, s));
       unsigned nb = (unsigned)ceil_div(nact, 256);
       k_pick<D><<<nb, 256, 0, s>>>(T, ain, nact, round);
       k_cavity<D><<<(unsigned)ceil_div(nact, 128), 128, 0, s>>>(T, ain, nact, round, S);
@@ -492,6 +494,11 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { failed = true; break; }
       if (c->status_host->error) return check_status(c, "insertion round");
       int nnew = h[0];
+      if (getenv("GDT_DEBUG")) {
+        int hc[4];
+        cudaMemcpy(hc, cnt + 4, 16, cudaMemcpyDeviceToHost);
+        fprintf(stderr, "round %u nact %d cand %d win %d\n", round, nact, hc[0], hc[2]);
+      }
       if (nnew == nact) {
         // no insertion anywhere: only possible when candidates overflowed their scratch
         if (c->status_host->overflow_cav && overflow_grow < 8) {

@@ -5,7 +5,7 @@
 
 namespace gdt {
 int run_pipeline(dt_ctx* c, const double* points, int64_t n, int dim, int k, double frac);
-int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out);
+int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out, const char* tag);
 void* stage_in(dt_ctx* c, const void* src, size_t bytes, const std::string& name, int* rc);
 int copy_out(dt_ctx* c, void* dst, const void* src, size_t bytes);
 bool is_device_ptr(const void* p);

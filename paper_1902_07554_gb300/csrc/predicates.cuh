@@ -360,16 +360,16 @@ static __device__ __noinline__ int exact_dispatch(int kind, int D, const double*
 // ---------------------------------------------------------------- point types
 template <int D> struct PT;
 template <> struct PT<2> { using T = double2; };
-template <> struct PT<3> { using T = double4; };
+template <> struct PT<3> { using T = double4_32a; };
 
 static __device__ __forceinline__ double cx(const double2& p) { return p.x; }
 static __device__ __forceinline__ double cy(const double2& p) { return p.y; }
 static __device__ __forceinline__ double cz(const double2&) { return 0.0; }
-static __device__ __forceinline__ double cx(const double4& p) { return p.x; }
-static __device__ __forceinline__ double cy(const double4& p) { return p.y; }
-static __device__ __forceinline__ double cz(const double4& p) { return p.z; }
+static __device__ __forceinline__ double cx(const double4_32a& p) { return p.x; }
+static __device__ __forceinline__ double cy(const double4_32a& p) { return p.y; }
+static __device__ __forceinline__ double cz(const double4_32a& p) { return p.z; }
 static __device__ __forceinline__ double comp(const double2& p, int c) { return c == 0 ? p.x : p.y; }
-static __device__ __forceinline__ double comp(const double4& p, int c) { return c == 0 ? p.x : (c == 1 ? p.y : p.z); }
+static __device__ __forceinline__ double comp(const double4_32a& p, int c) { return c == 0 ? p.x : (c == 1 ? p.y : p.z); }
 
 // Build TwoDiff pairs of (P[i] - Q) for `rows` points into dv (row*3+c)*2.
 template <typename P>
@@ -398,13 +398,13 @@ static __device__ __forceinline__ int orient2(double2 a, double2 b, double2 c) {
   return s ? s : orient2_exact(a, b, c);
 }
 
-static __device__ __noinline__ int orient3_exact(double4 a, double4 b, double4 c, double4 d) {
+static __device__ __noinline__ int orient3_exact(double4_32a a, double4_32a b, double4_32a c, double4_32a d) {
   double dv[3 * 3 * 2] = {0};
-  double4 rows[3] = {b, c, d};
+  double4_32a rows[3] = {b, c, d};
   diffs(dv, rows, 3, a, 3);
   return exact_dispatch(0, 3, dv, 18);
 }
-static __device__ __forceinline__ int orient3(double4 a, double4 b, double4 c, double4 d) {
+static __device__ __forceinline__ int orient3(double4_32a a, double4_32a b, double4_32a c, double4_32a d) {
   double b0 = b.x - a.x, b1 = b.y - a.y, b2 = b.z - a.z;
   double c0 = c.x - a.x, c1 = c.y - a.y, c2 = c.z - a.z;
   double d0 = d.x - a.x, d1 = d.y - a.y, d2 = d.z - a.z;
@@ -439,14 +439,14 @@ static __device__ __forceinline__ int insphere2_raw(double2 a, double2 b, double
   return s ? s : insphere2_exact(a, b, c, q);
 }
 
-static __device__ __noinline__ int insphere3_exact(double4 a, double4 b, double4 c, double4 d, double4 q) {
+static __device__ __noinline__ int insphere3_exact(double4_32a a, double4_32a b, double4_32a c, double4_32a d, double4_32a q) {
   double dv[4 * 3 * 2] = {0};
-  double4 rows[4] = {a, b, c, d};
+  double4_32a rows[4] = {a, b, c, d};
   diffs(dv, rows, 4, q, 3);
   return exact_dispatch(1, 3, dv, 24);
 }
 // > 0 iff q is strictly inside the circumsphere of the positively oriented abcd
-static __device__ __forceinline__ int insphere3_raw(double4 a, double4 b, double4 c, double4 d, double4 q) {
+static __device__ __forceinline__ int insphere3_raw(double4_32a a, double4_32a b, double4_32a c, double4_32a d, double4_32a q) {
   double ax = a.x - q.x, ay = a.y - q.y, az = a.z - q.z;
   double bx = b.x - q.x, by = b.y - q.y, bz = b.z - q.z;
   double cxx = c.x - q.x, cyy = c.y - q.y, czz = c.z - q.z;
@@ -480,13 +480,13 @@ static __device__ __forceinline__ int insphere3_raw(double4 a, double4 b, double
 static __device__ __forceinline__ int orient_p(const double2* P, const int* v) {
   return orient2(P[v[0]], P[v[1]], P[v[2]]);
 }
-static __device__ __forceinline__ int orient_p(const double4* P, const int* v) {
+static __device__ __forceinline__ int orient_p(const double4_32a* P, const int* v) {
   return orient3(P[v[0]], P[v[1]], P[v[2]], P[v[3]]);
 }
 static __device__ __forceinline__ int insphere_raw_p(const double2* P, const int* v, int q) {
   return insphere2_raw(P[v[0]], P[v[1]], P[v[2]], P[q]);
 }
-static __device__ __forceinline__ int insphere_raw_p(const double4* P, const int* v, int q) {
+static __device__ __forceinline__ int insphere_raw_p(const double4_32a* P, const int* v, int q) {
   return insphere3_raw(P[v[0]], P[v[1]], P[v[2]], P[v[3]], P[q]);
 }
 
@@ -541,22 +541,22 @@ static __device__ __forceinline__ int dot2_sign(double2 a, double2 b, double2 q)
 }
 
 // 3D: q on the plane of hull facet (a, b, c).
-static __device__ __noinline__ int coplanar_incircle3(double4 a, double4 b, double4 c, double4 q) {
+static __device__ __noinline__ int coplanar_incircle3(double4_32a a, double4_32a b, double4_32a c, double4_32a q) {
   double dv[6 * 3 * 2] = {0};
-  double4 rows[3] = {a, b, c};
+  double4_32a rows[3] = {a, b, c};
   diffs(dv, rows, 3, q, 3);
   return exact_dispatch(3, 3, dv, 18);
 }
-static __device__ __noinline__ int coplanar_orient3(double4 a, double4 b, double4 c, double4 x0, double4 x1,
-                                             double4 x2, double4 q) {
+static __device__ __noinline__ int coplanar_orient3(double4_32a a, double4_32a b, double4_32a c, double4_32a x0, double4_32a x1,
+                                             double4_32a x2, double4_32a q) {
   double dv[6 * 3 * 2] = {0};
-  double4 rows[6] = {a, b, c, x0, x1, x2};
+  double4_32a rows[6] = {a, b, c, x0, x1, x2};
   diffs(dv, rows, 6, q, 3);
   return exact_dispatch(4, 3, dv, 36);
 }
 
-static __device__ __noinline__ int ghost_coplanar3(const double4* P, const int* gid, const int* f, int q) {
-  double4 a = P[f[0]], b = P[f[1]], c = P[f[2]], x = P[q];
+static __device__ __noinline__ int ghost_coplanar3(const double4_32a* P, const int* gid, const int* f, int q) {
+  double4_32a a = P[f[0]], b = P[f[1]], c = P[f[2]], x = P[q];
   int r = coplanar_incircle3(a, b, c, x);
   if (r) return r > 0;
   // cocircular: perturbed lifts of f and q decide (largest global index first)
@@ -569,7 +569,7 @@ static __device__ __noinline__ int ghost_coplanar3(const double4* P, const int* 
       }
   for (int i = 0; i < 4; i++) {
     if (slot[i] < 0) return 0;
-    double4 t[3] = {a, b, c};
+    double4_32a t[3] = {a, b, c};
     t[slot[i]] = x;
     int o = coplanar_orient3(a, b, c, t[0], t[1], t[2], x);
     if (o) return o > 0;
@@ -594,7 +594,7 @@ static __device__ __forceinline__ bool in_conflict(const double2* P, const int* 
   int a = v[(g + 1) % 3], b = v[(g + 2) % 3];
   return dot2_sign(P[a], P[b], P[q]) < 0;
 }
-static __device__ __forceinline__ bool in_conflict(const double4* P, const int* gid, const int* v, int q) {
+static __device__ __forceinline__ bool in_conflict(const double4_32a* P, const int* gid, const int* v, int q) {
   int g = -1;
 #pragma unroll
   for (int i = 0; i < 4; i++) if (v[i] == INF_V) g = i;
