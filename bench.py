@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 divide-and-conquer Delaunay triangulation.
+
+Workload (default ``uniform3d_1m``): 3D, 1,000,000 points uniform in [0,1]^3
+(float64, seed 2), k = 16 partitions from a 0.5% sample (Alg. 1 + Alg. 2),
+grid border primitive, log edge weights.  One step = one full
+dt_triangulate: divide, 16 partial triangulations, border detection, border
+triangulation, hash merge and canonical output, all on the GPU.
+
+Printed (rank 0, one JSON line): Mpoints/s over the K timed steps (inputs
+resident in HBM, L2 flushed before every step), the same metric end to end
+through the C ABI from pinned host buffers (host<->device copies inside the
+timed region), the roofline of the dominant kernel measured live with CUDA
+events, the CPU oracle timed on a bounded sample, and the SM clocks seen.
+
+``--impl reference`` times the CPU oracle instead (the only reference that
+exists for this method: the paper ships no code), on a bounded sample.
+Multi-GPU (torchrun): every rank triangulates its own independent point set
+(replicas; no collective on the data path); value = all points / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pointsets  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+METRIC = "Mpoints/s for 3D DT on 1 GB300 vs plain path; p50/p99 latency under load"
+WORKLOADS = {
+    "uniform3d_1m": dict(n=1_000_000, dim=3, gen="uniform", seed=2, k=16, frac=0.005),
+    "clustered3d_4m": dict(n=4_000_000, dim=3, gen="clustered", seed=3, k=64, frac=0.005),
+    "uniform2d_10k": dict(n=10_000, dim=2, gen="uniform", seed=1, k=4, frac=0.01),
+    # a smaller case of the same shape, for profiler captures (a few GB on the device)
+    "uniform3d_200k": dict(n=200_000, dim=3, gen="uniform", seed=2, k=16, frac=0.005),
+}
+
+
+def gen_points(w, seed_offset=0):
+    if w["gen"] == "uniform":
+        return pointsets.uniform(w["n"], w["dim"], w["seed"] + seed_offset)
+    return pointsets.clustered(w["n"], w["seed"] + seed_offset)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for j, nm in enumerate(names):
+                if len(r) > 5 + j and r[5 + j].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """The CPU oracle (single-threaded C Bowyer-Watson) on a bounded sample of
+    the workload: the first m points, m chosen to take roughly budget_s."""
+    import oracle
+    P = gen_points(w)
+    m = min(w["n"], 20_000 if w["dim"] == 3 else 100_000)
+    t = time.perf_counter()
+    oracle.delaunay(P[:m])
+    dt = time.perf_counter() - t
+    # grow the sample once towards the budget
+    m2 = int(min(w["n"], m * max(1.0, budget_s / max(dt, 1e-3) * 0.8)))
+    if m2 > m:
+        t = time.perf_counter()
+        oracle.delaunay(P[:m2])
+        dt = time.perf_counter() - t
+        m = m2
+    return {"value": m / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m} of the {w['n']} workload points, one full DT by the C oracle, {dt:.2f} s"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    P = gen_points(w)
+    m = min(w["n"], 60_000 if w["dim"] == 3 else 300_000)
+    sample = P[:m]
+    for _ in range(args.warmup):
+        oracle.delaunay(sample[: m // 10])
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.delaunay(sample)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = m / (ms / 1e3) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": w["n"], "dim": w["dim"], "k": w["k"],
+                       "sample_frac": w["frac"], "reference_sample_points": m},
+            "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {m} of the {w['n']} workload points per step"},
+            "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform3d_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--divide", default="sample", choices=["sample", "kd"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1902_07554_gb300 import Triangulator
+    stream = torch.cuda.Stream(device=local)       # one explicit stream for torch and the library
+    torch.cuda.set_stream(stream)
+    tri = Triangulator(local, stream=stream.cuda_stream, divide=0 if args.divide == "sample" else 1, profile=0)
+    P = gen_points(w, seed_offset=rank)
+    n = w["n"]
+    P_dev = torch.from_numpy(P).to(f"cuda:{local}")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")   # > L2 (129 MB)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        tri.triangulate(P_dev, k=w["k"], sample_frac=w["frac"], fetch=False)
+
+    # ---------------- timed region: K steps on device-resident inputs
+    tri.configure(profile=1)
+    prof_tot = {}
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t0 = time.perf_counter()
+    step_ms = []
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tri.triangulate(P_dev, k=w["k"], sample_frac=w["frac"], fetch=False)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = tri.stats()
+        launches += st.launches
+        for kp in tri.kernel_profile():
+            a = prof_tot.setdefault(kp["name"], dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
+            for key in ("ms", "launches", "bytes", "flops"):
+                a[key] += kp[key]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms = sum(step_ms) / len(step_ms)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * n / (ms_max / 1e3) / 1e6
+    stats = tri.stats().as_dict()
+    tri.configure(profile=0)
+
+    # ---------------- end to end: pinned host buffers through the C ABI
+    P_pin = torch.from_numpy(P).pin_memory()
+    nout = tri.simplex_count()
+    out_pin = torch.empty((nout + 1024, w["dim"] + 1), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        tri.triangulate(P_pin, k=w["k"], sample_frac=w["frac"], fetch=False)
+        cnt = tri.simplex_count()
+        tri.simplices(out=out_pin[:cnt])
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    e2e_t = torch.tensor([e2e_step], dtype=torch.float64, device=f"cuda:{local}")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * n / (float(e2e_t.item()) / 1e3) / 1e6, "unit": "Mpoints/s",
+           "h2d_bytes_per_step": int(n * w["dim"] * 8), "d2h_bytes_per_step": int(cnt * (w["dim"] + 1) * 4),
+           "ms_per_step": e2e_step}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- roofline of the dominant kernel (live CUDA-event times)
+    peaks, peak_src = load_peaks()
+    dom = max(prof_tot.items(), key=lambda kv: kv[1]["ms"]) if prof_tot else None
+    roofline = None
+    if dom:
+        name, a = dom
+        per_launch_ms = a["ms"] / max(a["launches"], 1)
+        bytes_per_launch = a["bytes"] / max(a["launches"], 1)
+        achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                    "share_of_step": a["ms"] / sum(step_ms),
+                    "fp64_gflops": a["flops"] / (a["ms"] / 1e3) / 1e9 if a["ms"] > 0 else 0.0,
+                    "launches": a["launches"], "ms_per_launch": per_launch_ms,
+                    "bytes_per_launch": bytes_per_launch}
+    kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in prof_tot.items()}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "dim": w["dim"], "k": w["k"], "sample_frac": w["frac"],
+                   "divide": args.divide, "primitive": "grid", "weight": "log",
+                   "l2": "flushed before every step (256 MiB write); working set > L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "gpu_launches": int(launches),
+        "stats": {k: stats[k] for k in ("simplices", "eta", "border_vertices", "border_simplices", "imbalance",
+                                         "cv", "o_dt", "rounds_max", "exact_calls", "ms_phase")},
+        "kernels": kernels, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

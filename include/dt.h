@@ -83,8 +83,9 @@ typedef struct dt_config {
   uint64_t seed;         /* sample seed; default 1 */
   int base_threshold;    /* N of Alg. 1: run k = 1 when n / k < N; default 2048 */
   int validate;          /* 1: check every interior facet is locally Delaunay after the merge */
-  int cavity_cap;        /* initial per-insertion cavity capacity (simplices); default 64 */
-  int reserved[8];
+  int cavity_cap;        /* initial per-insertion cavity capacity (simplices); 0 = automatic */
+  int profile;           /* 1: time the insertion kernels with CUDA events (dt_get_kernel_profile) */
+  int reserved[7];
 } dt_config;
 
 typedef struct dt_stats {
@@ -107,7 +108,17 @@ typedef struct dt_stats {
                             border DT, merge, canonicalise, validate */
   int64_t partition_size_max;
   int64_t partition_size_min;
+  int64_t launches;      /* CUDA kernels this call launched */
 } dt_stats;
+
+/* One entry of the per-kernel profile (profile mode). */
+typedef struct dt_kernel_profile {
+  char name[32];
+  int64_t launches;
+  double ms;             /* summed CUDA-event time on the context stream */
+  double bytes;          /* algorithmic bytes (each record the kernel must touch, once) */
+  double flops;          /* FP64 operations of the predicate filters */
+} dt_kernel_profile;
 
 typedef struct dt_ctx dt_ctx;
 
@@ -159,6 +170,11 @@ DT_API int dt_get_sample_blocks(dt_ctx* ctx, int32_t* out, int64_t capacity);
 
 /* Border vertices of the last call: |vertices(B)| input indices, ascending. */
 DT_API int dt_get_border_vertices(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Per-kernel profile of the last dt_triangulate (filled only when the
+ * configuration has profile = 1): up to max entries into out (host), the
+ * number available in *count. */
+DT_API int dt_get_kernel_profile(dt_ctx* ctx, dt_kernel_profile* out, int max, int* count);
 
 /* Human-readable description of the last error on this context (never NULL). */
 DT_API const char* dt_last_error(dt_ctx* ctx);

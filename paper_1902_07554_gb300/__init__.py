@@ -47,7 +47,12 @@ class Config(ctypes.Structure):
                 ("lp_rounds", ctypes.c_int), ("epsilon", ctypes.c_double),
                 ("grid_cell", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("base_threshold", ctypes.c_int), ("validate", ctypes.c_int),
-                ("cavity_cap", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("cv", ctypes.c_double), ("o_dt", ctypes.c_double), ("cut_weight", ctypes.c_int64),
                 ("rounds_max", ctypes.c_int32), ("exact_calls", ctypes.c_int32),
                 ("ms_total", ctypes.c_double), ("ms_phase", ctypes.c_double * 8),
-                ("partition_size_max", ctypes.c_int64), ("partition_size_min", ctypes.c_int64)]
+                ("partition_size_max", ctypes.c_int64), ("partition_size_min", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         d = {}
@@ -105,6 +111,7 @@ def load_library(build: bool = True):
         "dt_eval_predicates": ([p, p, i64, i32, p, i32, p, i64, p], i32),
         "dt_label_points": ([p, p, i64, i32, p, p, p, i64, p], i32),
         "dt_partition_graph": ([p, p, i64, i32, p, p, i64, i32, dbl, i32, p], i32),
+        "dt_get_kernel_profile": ([p, p, i32, p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -209,6 +216,14 @@ class Triangulator:
         s = Stats()
         self._check(self.L.dt_get_stats(self.ctx, ctypes.byref(s)))
         return s
+
+    def kernel_profile(self):
+        cnt = ctypes.c_int()
+        self._check(self.L.dt_get_kernel_profile(self.ctx, None, 0, ctypes.byref(cnt)))
+        arr = (KernelProfile * max(cnt.value, 1))()
+        self._check(self.L.dt_get_kernel_profile(self.ctx, arr, cnt.value, ctypes.byref(cnt)))
+        return [dict(name=a.name.decode(), launches=a.launches, ms=a.ms, bytes=a.bytes, flops=a.flops)
+                for a in arr[:cnt.value]]
 
     def labels(self):
         n = self.stats().n

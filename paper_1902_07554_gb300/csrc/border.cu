@@ -407,7 +407,7 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
   CUDA_OK(cudaMemsetAsync(vflag, 0, std::max<int64_t>(n, 1), s));
   CUDA_OK(cudaMemsetAsync(cnt, 0, 16, s));
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
-  k_flag_bad_partitions<<<g, 256, 0, s>>>(pinst, parts.inst_status, n, vflag);
+  k_flag_bad_partitions<<<g, 256, (++c->launches, 0), s>>>(pinst, parts.inst_status, n, vflag);
   BorderArgs A;
   A.tv = (const int4*)parts.tv;
   A.toff = parts.toff;
@@ -424,10 +424,10 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
   memset(&A.G, 0, sizeof(A.G));
   // per-partition boxes (bbox primitive and the grid's extent)
   CUDA_OK(cudaMemsetAsync(ubox, 0, 8 * 6 * (size_t)k, s));
-  k_init_ubox<<<ceil_div(6 * k, 128), 128, 0, s>>>(ubox, k);
-  if (dim == 2) k_part_boxes<2><<<g, 256, 0, s>>>((const double2*)Ps, pinst, n, ubox);
-  else k_part_boxes<3><<<g, 256, 0, s>>>((const double4_32a*)Ps, pinst, n, ubox);
-  k_boxes_to_double<<<ceil_div(6 * k, 128), 128, 0, s>>>(ubox, k, boxes);
+  k_init_ubox<<<ceil_div(6 * k, 128), 128, (++c->launches, 0), s>>>(ubox, k);
+  if (dim == 2) k_part_boxes<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)Ps, pinst, n, ubox);
+  else k_part_boxes<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)Ps, pinst, n, ubox);
+  k_boxes_to_double<<<ceil_div(6 * k, 128), 128, (++c->launches, 0), s>>>(ubox, k, boxes);
   if (prim == DT_PRIM_GRID) {
     if (k > 64) return set_err(c, DT_E_ARG, "the grid primitive supports k <= 64");
     std::vector<double> hb(6 * (size_t)k);
@@ -481,18 +481,18 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
     if (!mask) return set_err(c, DT_E_NOMEM, "grid masks");
     CUDA_OK(cudaMemsetAsync(mask, 0, 8 * (size_t)total, s));
     G.mask = mask;
-    if (dim == 2) k_occupy<2><<<g, 256, 0, s>>>((const double2*)Ps, pinst, n, G, mask);
-    else k_occupy<3><<<g, 256, 0, s>>>((const double4_32a*)Ps, pinst, n, G, mask);
+    if (dim == 2) k_occupy<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)Ps, pinst, n, G, mask);
+    else k_occupy<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)Ps, pinst, n, G, mask);
     for (int l = 1; l < G.levels; l++) {
       long long cells = (long long)G.dims[l][0] * G.dims[l][1] * G.dims[l][2];
       unsigned gl = (unsigned)ceil_div<long long>(cells, 256);
-      if (dim == 2) k_pyramid<2><<<gl, 256, 0, s>>>(G, l, mask);
-      else k_pyramid<3><<<gl, 256, 0, s>>>(G, l, mask);
+      if (dim == 2) k_pyramid<2><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask);
+      else k_pyramid<3><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask);
     }
   }
   unsigned gs = (unsigned)ceil_div<int64_t>(parts.total_slots, 128);
-  if (dim == 2) k_border<2><<<gs, 128, 0, s>>>((const double2*)Ps, A);
-  else k_border<3><<<gs, 128, 0, s>>>((const double4_32a*)Ps, A);
+  if (dim == 2) k_border<2><<<gs, 128, (++c->launches, 0), s>>>((const double2*)Ps, A);
+  else k_border<3><<<gs, 128, (++c->launches, 0), s>>>((const double4_32a*)Ps, A);
   int h = 0;
   CUDA_OK(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));

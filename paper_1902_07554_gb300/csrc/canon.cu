@@ -112,13 +112,13 @@ int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64
   CUDA_OK(cudaMemsetAsync(bc, 0, 4 * nbuckets, s));
   CUDA_OK(cudaMemsetAsync(bf, 0, 4 * nbuckets, s));
   unsigned g = (unsigned)ceil_div<int64_t>(nrows, 256);
-  k_bucket_count<<<g, 256, 0, s>>>(rows, nrows, bc);
+  k_bucket_count<<<g, 256, (++c->launches, 0), s>>>(rows, nrows, bc);
   int rc = exclusive_scan_i32(c, bc, bs, nbuckets, nullptr);
   if (rc) return rc;
-  k_bucket_scatter<<<g, 256, 0, s>>>(rows, nrows, bs, bf, tmp);
+  k_bucket_scatter<<<g, 256, (++c->launches, 0), s>>>(rows, nrows, bs, bf, tmp);
   unsigned gb = (unsigned)ceil_div<int64_t>(nbuckets, 128);
-  if (dim == 2) k_bucket_sort<2><<<gb, 128, 0, s>>>(tmp, bs, bc, nbuckets, o);
-  else k_bucket_sort<3><<<gb, 128, 0, s>>>(tmp, bs, bc, nbuckets, o);
+  if (dim == 2) k_bucket_sort<2><<<gb, 128, (++c->launches, 0), s>>>(tmp, bs, bc, nbuckets, o);
+  else k_bucket_sort<3><<<gb, 128, (++c->launches, 0), s>>>(tmp, bs, bc, nbuckets, o);
   return 0;
 }
 
@@ -141,10 +141,10 @@ int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsign
   unsigned g = (unsigned)ceil_div<int64_t>(ns, 256);
   if (mode && !flag) mode = 0;
   if (run.dim == 2)
-    k_collect_finite<2><<<g, 256, 0, s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
+    k_collect_finite<2><<<g, 256, (++c->launches, 0), s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
                                           flag, mode, r, cnt);
   else
-    k_collect_finite<3><<<g, 256, 0, s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
+    k_collect_finite<3><<<g, 256, (++c->launches, 0), s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
                                           flag, mode, r, cnt);
   int h = 0;
   CUDA_OK(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s));

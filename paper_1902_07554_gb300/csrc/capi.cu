@@ -66,6 +66,7 @@ extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_c
     return DT_E_NOMEM;
   }
   for (int i = 0; i < 16; i++) cudaEventCreate(&c->ev[i]);
+  for (int i = 0; i < 16; i++) cudaEventCreate(&c->pev[i]);
   memset(&c->stats, 0, sizeof(c->stats));
   *out = c;
   return DT_OK;
@@ -87,6 +88,7 @@ extern "C" void dt_destroy(dt_ctx* c) {
   if (c->status_host) cudaFreeHost(c->status_host);
   if (c->counters_host) cudaFreeHost(c->counters_host);
   for (int i = 0; i < 16; i++) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (int i = 0; i < 16; i++) if (c->pev[i]) cudaEventDestroy(c->pev[i]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -179,11 +181,11 @@ int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_o
   CUDA_OK(cudaMemsetAsync(table, 0xff, 4 * (size_t)tsize, c->stream));
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
   if (dim == 2) {
-    k_pack_points<2><<<g, 256, 0, c->stream>>>(src, n, (double2*)P, flags);
-    k_dup_check<2><<<g, 256, 0, c->stream>>>((const double2*)P, n, table, tsize - 1, flags + 1);
+    k_pack_points<2><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double2*)P, flags);
+    k_dup_check<2><<<g, 256, (++c->launches, 0), c->stream>>>((const double2*)P, n, table, tsize - 1, flags + 1);
   } else {
-    k_pack_points<3><<<g, 256, 0, c->stream>>>(src, n, (double4_32a*)P, flags);
-    k_dup_check<3><<<g, 256, 0, c->stream>>>((const double4_32a*)P, n, table, tsize - 1, flags + 1);
+    k_pack_points<3><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double4_32a*)P, flags);
+    k_dup_check<3><<<g, 256, (++c->launches, 0), c->stream>>>((const double4_32a*)P, n, table, tsize - 1, flags + 1);
   }
   int h[2];
   CUDA_OK(cudaMemcpyAsync(h, flags, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -214,6 +216,8 @@ extern "C" int dt_triangulate(dt_ctx* c, const double* points, int64_t n, int di
   c->stats.n = n;
   c->stats.dim = dim;
   c->stats.k = 1;
+  c->kprof.clear();
+  long long l0 = c->launches;
   cudaEventRecord(c->ev[0], c->stream);
   int rc = run_pipeline(c, points, n, dim, k, sample_frac);
   if (rc) return rc;
@@ -228,6 +232,22 @@ extern "C" int dt_triangulate(dt_ctx* c, const double* points, int64_t n, int di
   if (rc) return rc;
   c->stats.exact_calls = (int32_t)std::min<unsigned long long>(calls, 0x7fffffffull);
   c->stats.simplices = c->nout;
+  c->stats.launches = c->launches - l0;
+  return DT_OK;
+}
+
+extern "C" int dt_get_kernel_profile(dt_ctx* c, dt_kernel_profile* out, int max, int* count) {
+  if (!c || !count) return DT_E_ARG;
+  *count = (int)c->kprof.size();
+  if (!out) return DT_OK;
+  for (int i = 0; i < max && i < (int)c->kprof.size(); i++) {
+    memset(&out[i], 0, sizeof(out[i]));
+    strncpy(out[i].name, c->kprof[i].name, 31);
+    out[i].launches = c->kprof[i].launches;
+    out[i].ms = c->kprof[i].ms;
+    out[i].bytes = c->kprof[i].bytes;
+    out[i].flops = c->kprof[i].flops;
+  }
   return DT_OK;
 }
 
@@ -348,21 +368,21 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
   if (gid) {
     const long long* g64 = (const long long*)stage_in(c, gid, 8 * n, "pred.g64", &rc);
     if (rc) return rc;
-    k_i64_to_i32<<<g, 256, 0, c->stream>>>(g64, g32, n);
+    k_i64_to_i32<<<g, 256, (++c->launches, 0), c->stream>>>(g64, g32, n);
   } else {
-    k_iota<<<g, 256, 0, c->stream>>>(g32, n, 0);
+    k_iota<<<g, 256, (++c->launches, 0), c->stream>>>(g32, n, 0);
   }
   unsigned gm = (unsigned)ceil_div<int64_t>(m, 128);
   if (dim == 2) {
-    k_pack_points<2><<<g, 256, 0, c->stream>>>(src, n, (double2*)P, flags);
-    k_eval_pred<2><<<gm, 128, 0, c->stream>>>((const double2*)P, g32, kind, tup, m, (int)n, o, flags + 1);
+    k_pack_points<2><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double2*)P, flags);
+    k_eval_pred<2><<<gm, 128, (++c->launches, 0), c->stream>>>((const double2*)P, g32, kind, tup, m, (int)n, o, flags + 1);
   } else {
-    k_pack_points<3><<<g, 256, 0, c->stream>>>(src, n, (double4_32a*)P, flags);
-    k_eval_pred<3><<<gm, 128, 0, c->stream>>>((const double4_32a*)P, g32, kind, tup, m, (int)n, o, flags + 1);
+    k_pack_points<3><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double4_32a*)P, flags);
+    k_eval_pred<3><<<gm, 128, (++c->launches, 0), c->stream>>>((const double4_32a*)P, g32, kind, tup, m, (int)n, o, flags + 1);
   }
   unsigned long long* ctr = (unsigned long long*)pool_get(c, "pred.ctr", 32);
   if (!ctr) return set_err(c, DT_E_NOMEM, "predicate counters");
-  k_read_pred_counters_capi<<<1, 1, 0, c->stream>>>(ctr, (int*)(ctr + 1));
+  k_read_pred_counters_capi<<<1, 1, (++c->launches, 0), c->stream>>>(ctr, (int*)(ctr + 1));
   int h[2];
   unsigned long long hc[2];
   CUDA_OK(cudaMemcpyAsync(h, flags, 8, cudaMemcpyDeviceToHost, c->stream));

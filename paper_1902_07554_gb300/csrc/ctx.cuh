@@ -20,6 +20,11 @@ struct dt_ctx {
   gdt::DevStatus* status_host = nullptr; // pinned mirror
   int* counters_host = nullptr;          // pinned scratch for small read-backs (64 ints)
   cudaEvent_t ev[16];
+  cudaEvent_t pev[16];                   // per-kernel profiling events
+  long long launches = 0;                // kernels launched by this context (all calls)
+  // per-kernel profile of the last call (profile mode)
+  struct KProf { const char* name; long long launches; double ms, bytes, flops; };
+  std::vector<KProf> kprof;
   // last result
   int dim = 0;
   int64_t n = 0;
@@ -53,6 +58,9 @@ int check_status(dt_ctx* c, const char* where);
 // Generic device helpers (defined in util.cu).
 int exclusive_scan_i32(dt_ctx* c, const int* in, int* out, int64_t n, int* total_host);
 int exclusive_scan_i64(dt_ctx* c, const long long* in, long long* out, int64_t n);
+
+// Accumulates a per-kernel profile entry (profile mode).
+void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops);
 
 // Engine (engine.cu).
 int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,

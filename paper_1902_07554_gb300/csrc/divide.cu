@@ -87,14 +87,14 @@ int select_sample(dt_ctx* c, int64_t n, int64_t eta, uint64_t seed, int* ids) {
   unsigned long long sm = splitmix64(seed);
   unsigned g = (unsigned)std::min<int64_t>(ceil_div<int64_t>(n, 256), 152 * 8);
   for (int shift = 56; shift >= 0; shift -= 8) {
-    k_sel_hist<<<g, 256, 0, s>>>(n, sm, st, shift, hist);
-    k_sel_pick<<<1, 1, 0, s>>>(st, hist, shift);
+    k_sel_hist<<<g, 256, (++c->launches, 0), s>>>(n, sm, st, shift, hist);
+    k_sel_pick<<<1, 1, (++c->launches, 0), s>>>(st, hist, shift);
   }
   unsigned gn = (unsigned)ceil_div<int64_t>(n, 256);
-  k_sel_flag<<<gn, 256, 0, s>>>(n, sm, st, flag);
+  k_sel_flag<<<gn, 256, (++c->launches, 0), s>>>(n, sm, st, flag);
   int rc = exclusive_scan_i32(c, flag, pos, n, nullptr);
   if (rc) return rc;
-  k_compact_idx<<<gn, 256, 0, s>>>(flag, pos, n, ids);
+  k_compact_idx<<<gn, 256, (++c->launches, 0), s>>>(flag, pos, n, ids);
   return 0;
 }
 
@@ -106,8 +106,8 @@ __global__ void k_gather_pts(const typename PT<D>::T* P, const int* ids, int64_t
 
 int gather_points(dt_ctx* c, int dim, const void* P, const int* ids, int64_t m, void* out) {
   unsigned g = (unsigned)ceil_div<int64_t>(std::max<int64_t>(m, 1), 256);
-  if (dim == 2) k_gather_pts<2><<<g, 256, 0, c->stream>>>((const double2*)P, ids, m, (double2*)out);
-  else k_gather_pts<3><<<g, 256, 0, c->stream>>>((const double4_32a*)P, ids, m, (double4_32a*)out);
+  if (dim == 2) k_gather_pts<2><<<g, 256, (++c->launches, 0), c->stream>>>((const double2*)P, ids, m, (double2*)out);
+  else k_gather_pts<3><<<g, 256, (++c->launches, 0), c->stream>>>((const double4_32a*)P, ids, m, (double4_32a*)out);
   return 0;
 }
 
@@ -230,8 +230,8 @@ __global__ void k_fill_csr(const int2* E, const long long* w, int64_t m, const i
 }
 
 int graph_bbox(dt_ctx* c, int dim, const void* PS, int64_t eta, double* box) {
-  if (dim == 2) k_bbox<2><<<1, 256, 0, c->stream>>>((const double2*)PS, eta, box);
-  else k_bbox<3><<<1, 256, 0, c->stream>>>((const double4_32a*)PS, eta, box);
+  if (dim == 2) k_bbox<2><<<1, 256, (++c->launches, 0), c->stream>>>((const double2*)PS, eta, box);
+  else k_bbox<3><<<1, 256, (++c->launches, 0), c->stream>>>((const double4_32a*)PS, eta, box);
   return 0;
 }
 
@@ -247,10 +247,10 @@ int build_csr(dt_ctx* c, SampleGraph& G) {
   CUDA_OK(cudaMemsetAsync(deg, 0, 4 * (eta + 1), s));
   CUDA_OK(cudaMemsetAsync(fill, 0, 4 * (eta + 1), s));
   unsigned g = (unsigned)ceil_div<int64_t>(std::max<int64_t>(G.m, 1), 256);
-  if (G.m) k_degree<<<g, 256, 0, s>>>(G.E, G.m, deg);
+  if (G.m) k_degree<<<g, 256, (++c->launches, 0), s>>>(G.E, G.m, deg);
   int rc = exclusive_scan_i32(c, deg, G.rowptr, eta + 1, nullptr);
   if (rc) return rc;
-  if (G.m) k_fill_csr<<<g, 256, 0, s>>>(G.E, G.w, G.m, G.rowptr, fill, G.col, G.cw);
+  if (G.m) k_fill_csr<<<g, 256, (++c->launches, 0), s>>>(G.E, G.w, G.m, G.rowptr, fill, G.col, G.cw);
   return 0;
 }
 
@@ -275,17 +275,17 @@ int sample_graph(dt_ctx* c, const EngineRun& run, const void* PS, int dim, int k
   CUDA_OK(cudaMemsetAsync(ucount, 0, 4 * (eta + 1), s));
   CUDA_OK(cudaMemsetAsync(ufill, 0, 4 * (eta + 1), s));
   unsigned g = (unsigned)ceil_div(std::max(hi - lo, 1), 256);
-  if (dim == 2) k_emit_edges<2><<<g, 256, 0, s>>>((const int4*)run.tv, lo, hi, raw, cnt, ucount);
-  else k_emit_edges<3><<<g, 256, 0, s>>>((const int4*)run.tv, lo, hi, raw, cnt, ucount);
+  if (dim == 2) k_emit_edges<2><<<g, 256, (++c->launches, 0), s>>>((const int4*)run.tv, lo, hi, raw, cnt, ucount);
+  else k_emit_edges<3><<<g, 256, (++c->launches, 0), s>>>((const int4*)run.tv, lo, hi, raw, cnt, ucount);
   int nraw = 0;
   CUDA_OK(cudaMemcpyAsync(&nraw, cnt, 4, cudaMemcpyDeviceToHost, s));
   int rc = exclusive_scan_i32(c, ucount, ustart, eta + 1, nullptr);
   if (rc) return rc;
   CUDA_OK(cudaStreamSynchronize(s));
   unsigned ge = (unsigned)ceil_div<int64_t>(std::max(nraw, 1), 256);
-  k_bucket_edges<<<ge, 256, 0, s>>>(raw, nraw, ustart, ufill, vout);
+  k_bucket_edges<<<ge, 256, (++c->launches, 0), s>>>(raw, nraw, ustart, ufill, vout);
   unsigned gu = (unsigned)ceil_div<int64_t>(eta, 128);
-  k_unique_buckets<<<gu, 128, 0, s>>>(vout, ustart, ucount, eta);
+  k_unique_buckets<<<gu, 128, (++c->launches, 0), s>>>(vout, ustart, ucount, eta);
   int m = 0;
   rc = exclusive_scan_i32(c, ucount, upos, eta + 1, &m);
   if (rc) return rc;
@@ -293,13 +293,13 @@ int sample_graph(dt_ctx* c, const EngineRun& run, const void* PS, int dim, int k
   G.E = (int2*)pool_get(c, "g.E", 8 * std::max(m, 1));
   G.w = (long long*)pool_get(c, "g.w", 8 * std::max(m, 1));
   if (!G.E || !G.w) return set_err(c, DT_E_NOMEM, "graph edges");
-  k_write_unique<<<gu, 128, 0, s>>>(vout, ustart, ucount, upos, eta, G.E);
-  if (dim == 2) k_bbox<2><<<1, 256, 0, s>>>((const double2*)PS, eta, G.box);
-  else k_bbox<3><<<1, 256, 0, s>>>((const double4_32a*)PS, eta, G.box);
+  k_write_unique<<<gu, 128, (++c->launches, 0), s>>>(vout, ustart, ucount, upos, eta, G.E);
+  if (dim == 2) k_bbox<2><<<1, 256, (++c->launches, 0), s>>>((const double2*)PS, eta, G.box);
+  else k_bbox<3><<<1, 256, (++c->launches, 0), s>>>((const double4_32a*)PS, eta, G.box);
   unsigned gm = (unsigned)ceil_div<int64_t>(std::max(m, 1), 256);
   if (m) {
-    if (dim == 2) k_edge_weights<2><<<gm, 256, 0, s>>>((const double2*)PS, G.E, m, G.box, kind, G.w);
-    else k_edge_weights<3><<<gm, 256, 0, s>>>((const double4_32a*)PS, G.E, m, G.box, kind, G.w);
+    if (dim == 2) k_edge_weights<2><<<gm, 256, (++c->launches, 0), s>>>((const double2*)PS, G.E, m, G.box, kind, G.w);
+    else k_edge_weights<3><<<gm, 256, (++c->launches, 0), s>>>((const double4_32a*)PS, G.E, m, G.box, kind, G.w);
   }
   return build_csr(c, G);
 }
@@ -416,23 +416,23 @@ int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, d
     return set_err(c, DT_E_NOMEM, "partition buffers");
   int bits = dim == 2 ? 16 : 10;
   unsigned g = (unsigned)ceil_div<int64_t>(eta, 256);
-  if (dim == 2) k_hilbert<2><<<g, 256, 0, s>>>((const double2*)PS, eta, G.box, bits, keys, idx);
-  else k_hilbert<3><<<g, 256, 0, s>>>((const double4_32a*)PS, eta, G.box, bits, keys, idx);
+  if (dim == 2) k_hilbert<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)PS, eta, G.box, bits, keys, idx);
+  else k_hilbert<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)PS, eta, G.box, bits, keys, idx);
   int rc = radix_sort_pairs<uint32_t, int>(c, keys, idx, eta, bits * dim, "p.sort");
   if (rc) return rc;
-  k_initial_blocks<<<g, 256, 0, s>>>(idx, eta, k, block);
+  k_initial_blocks<<<g, 256, (++c->launches, 0), s>>>(idx, eta, k, block);
   int lmin, lmax;
   partition_bounds(eta, k, eps, &lmin, &lmax);
   for (int r = 0; r < rounds; r++) {
     rc = group_rank(c, block, eta, rankB, sizes, k);
     if (rc) return rc;
-    k_lp_propose<<<g, 256, 0, s>>>(G.rowptr, G.col, G.cw, block, eta, r & 1, target);
-    k_lp_source<<<g, 256, 0, s>>>(target, block, eta, source);
+    k_lp_propose<<<g, 256, (++c->launches, 0), s>>>(G.rowptr, G.col, G.cw, block, eta, r & 1, target);
+    k_lp_source<<<g, 256, (++c->launches, 0), s>>>(target, block, eta, source);
     rc = group_rank(c, target, eta, rankT, nullptr, k);
     if (rc) return rc;
     rc = group_rank(c, source, eta, rankS, nullptr, k);
     if (rc) return rc;
-    k_lp_apply<<<g, 256, 0, s>>>(target, rankT, rankS, sizes, eta, lmin, lmax, block);
+    k_lp_apply<<<g, 256, (++c->launches, 0), s>>>(target, rankT, rankS, sizes, eta, lmin, lmax, block);
   }
   return 0;
 }
@@ -448,7 +448,7 @@ int cut_weight(dt_ctx* c, const SampleGraph& G, const int* block, long long* out
   if (!d) return set_err(c, DT_E_NOMEM, "cut");
   CUDA_OK(cudaMemsetAsync(d, 0, 8, c->stream));
   if (G.m)
-    k_cut_weight<<<(unsigned)ceil_div<int64_t>(G.m, 256), 256, 0, c->stream>>>(G.E, G.w, G.m, block, d);
+    k_cut_weight<<<(unsigned)ceil_div<int64_t>(G.m, 256), 256, (++c->launches, 0), c->stream>>>(G.E, G.w, G.m, block, d);
   unsigned long long h = 0;
   CUDA_OK(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(cudaStreamSynchronize(c->stream));
@@ -537,8 +537,8 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
   // start grid over the bounding box of all points, about m/4 cells
   double* box = (double*)pool_get(c, "lw.box", 48);
   if (!box) return set_err(c, DT_E_NOMEM, "label box");
-  if (dim == 2) k_bbox<2><<<1, 256, 0, s>>>((const double2*)P, n, box);
-  else k_bbox<3><<<1, 256, 0, s>>>((const double4_32a*)P, n, box);
+  if (dim == 2) k_bbox<2><<<1, 256, (++c->launches, 0), s>>>((const double2*)P, n, box);
+  else k_bbox<3><<<1, 256, (++c->launches, 0), s>>>((const double4_32a*)P, n, box);
   double hb[6];
   CUDA_OK(cudaMemcpyAsync(hb, box, 48, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
@@ -561,21 +561,21 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
   int* cv1 = (int*)pool_get(c, "lw.cv1", 4 * ncell);
   if (!cv0 || !cv1) return set_err(c, DT_E_NOMEM, "label grid");
   unsigned gm = (unsigned)ceil_div<int64_t>(m, 256);
-  k_fill_int<<<(unsigned)ceil_div<int64_t>(ncell, 256), 256, 0, s>>>(cv0, ncell, 0x7fffffff);
-  if (dim == 2) k_seed_cells<2><<<gm, 256, 0, s>>>((const double2*)S, m, sg, cv0);
-  else k_seed_cells<3><<<gm, 256, 0, s>>>((const double4_32a*)S, m, sg, cv0);
+  k_fill_int<<<(unsigned)ceil_div<int64_t>(ncell, 256), 256, (++c->launches, 0), s>>>(cv0, ncell, 0x7fffffff);
+  if (dim == 2) k_seed_cells<2><<<gm, 256, (++c->launches, 0), s>>>((const double2*)S, m, sg, cv0);
+  else k_seed_cells<3><<<gm, 256, (++c->launches, 0), s>>>((const double4_32a*)S, m, sg, cv0);
   unsigned gc = (unsigned)ceil_div<int64_t>(ncell, 256);
   for (int pass = 0; pass < 6; pass++) {
-    if (dim == 2) k_dilate<2><<<gc, 256, 0, s>>>(cv0, cv1, sg, ncell);
-    else k_dilate<3><<<gc, 256, 0, s>>>(cv0, cv1, sg, ncell);
+    if (dim == 2) k_dilate<2><<<gc, 256, (++c->launches, 0), s>>>(cv0, cv1, sg, ncell);
+    else k_dilate<3><<<gc, 256, (++c->launches, 0), s>>>(cv0, cv1, sg, ncell);
     std::swap(cv0, cv1);
   }
   unsigned gn = (unsigned)ceil_div<int64_t>(n, 128);
   if (dim == 2)
-    k_label_walk<2><<<gn, 128, 0, s>>>((const double2*)P, n, (const double2*)S, srank, G.rowptr, G.col, block, cv0, sg,
+    k_label_walk<2><<<gn, 128, (++c->launches, 0), s>>>((const double2*)P, n, (const double2*)S, srank, G.rowptr, G.col, block, cv0, sg,
                                        m, label, nearest, c->status);
   else
-    k_label_walk<3><<<gn, 128, 0, s>>>((const double4_32a*)P, n, (const double4_32a*)S, srank, G.rowptr, G.col, block, cv0, sg,
+    k_label_walk<3><<<gn, 128, (++c->launches, 0), s>>>((const double4_32a*)P, n, (const double4_32a*)S, srank, G.rowptr, G.col, block, cv0, sg,
                                        m, label, nearest, c->status);
   return 0;
 }
@@ -647,14 +647,14 @@ int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label) {
     }
     CUDA_OK(cudaMemcpyAsync(tabs, hs.data(), 4 * 4 * (size_t)k, cudaMemcpyHostToDevice, s));
     int cdim = depth % dim;
-    if (dim == 2) k_kd_keys<2><<<g, 256, 0, s>>>((const double2*)P, n, cdim, keys, idx);
-    else k_kd_keys<3><<<g, 256, 0, s>>>((const double4_32a*)P, n, cdim, keys, idx);
+    if (dim == 2) k_kd_keys<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)P, n, cdim, keys, idx);
+    else k_kd_keys<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)P, n, cdim, keys, idx);
     int rc = radix_sort_pairs<unsigned long long, int>(c, keys, idx, n, 64, "kd.s1");
     if (rc) return rc;
-    k_kd_nodekeys<<<g, 256, 0, s>>>(idx, label, n, nkeys);
+    k_kd_nodekeys<<<g, 256, (++c->launches, 0), s>>>(idx, label, n, nkeys);
     rc = radix_sort_pairs<uint32_t, int>(c, nkeys, idx, n, nbits, "kd.s2");
     if (rc) return rc;
-    k_kd_assign<<<g, 256, 0, s>>>(idx, n, tabs, tabs + k, tabs + 2 * k, tabs + 3 * k, label);
+    k_kd_assign<<<g, 256, (++c->launches, 0), s>>>(idx, n, tabs, tabs + k, tabs + 2 * k, tabs + 3 * k, label);
     nodes = next;
     CUDA_OK(cudaStreamSynchronize(s));   // host tables are reused next level
   }
@@ -695,8 +695,8 @@ int scatter_by_label(dt_ctx* c, int dim, const void* P, const int* label, int64_
   if (poff[k] != n) return set_err(c, DT_E_INTERNAL, "labels out of range");
   CUDA_OK(cudaMemcpyAsync(dpoff, hp.data(), 4 * (k + 1), cudaMemcpyHostToDevice, s));
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
-  if (dim == 2) k_scatter<2><<<g, 256, 0, s>>>((const double2*)P, label, rank, dpoff, n, (double2*)Ps, gid, pinst, nullptr);
-  else k_scatter<3><<<g, 256, 0, s>>>((const double4_32a*)P, label, rank, dpoff, n, (double4_32a*)Ps, gid, pinst, nullptr);
+  if (dim == 2) k_scatter<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)P, label, rank, dpoff, n, (double2*)Ps, gid, pinst, nullptr);
+  else k_scatter<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)P, label, rank, dpoff, n, (double4_32a*)Ps, gid, pinst, nullptr);
   return 0;
 }
 

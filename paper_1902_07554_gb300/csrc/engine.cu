@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 
 #include "ctx.cuh"
 
@@ -9,8 +10,12 @@ namespace gdt {
 
 constexpr int TAGBIT = (int)0x80000000;
 
+// Candidate key of point p in a round: the round in the high word (older
+// claims compare smaller), a per-round pseudo-random priority in the low word
+// (p -> p ^ c and fmix32 are bijections, so keys are unique within a round).
 __device__ __forceinline__ unsigned long long mkkey(unsigned round, int p) {
-  return ((unsigned long long)round << 32) | (unsigned long long)fmix32((uint32_t)p);
+  return ((unsigned long long)round << 32) |
+         (unsigned long long)fmix32((uint32_t)p ^ (round * 0x9E3779B9u));
 }
 __device__ __forceinline__ int get4(const int4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -161,7 +166,7 @@ __global__ void k_pick(TriView<D> T, const int* act, int nact, unsigned round) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nact) return;
   int p = act[idx];
-  atomicMax(&T.claimA[T.loc[p]], mkkey(round, p));
+  atomicMax(&T.claimC[T.loc[p]], mkkey(round, p));
 }
 
 enum { CAND_OK = 0, CAND_LOST = 1, CAND_OVER = 2 };
@@ -174,14 +179,25 @@ __global__ void __launch_bounds__(128) k_cavity(TriView<D> T, const int* act, in
   int p = act[idx];
   unsigned long long key = mkkey(round, p);
   int t0 = T.loc[p];
-  if (*((volatile unsigned long long*)&T.claimA[t0]) != key) return;   // not its simplex's nominee
+  // the pick left, in claimC, the strongest key of the points in each simplex
+  if (*((volatile unsigned long long*)&T.claimC[t0]) != key) return;   // not its simplex's nominee
+  // Every neighbour of t0 lies in p's region or ring; a stronger nominee in a
+  // neighbour has that neighbour in its own region, so p would lose: skip.
+  {
+    int4 nn0 = T.tn[t0];
+    for (int i = 0; i <= D; i++) {
+      int u = nb_simplex(get4(nn0, i));
+      if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) return;
+    }
+  }
   int slot = atomicAdd(S.count, 1);
   if (slot >= S.cap) return;
   S.cand[slot] = p;
   int* C = S.cav + (int64_t)slot * S.capC;
   int* B = S.bnd + (int64_t)slot * S.capB;
   int nc = 0, nbd = 0, status = CAND_OK;
-  unsigned long long o = atomicMax(&T.claimC[t0], key);
+  unsigned long long pbytes = sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1), ptests = 0;
+  unsigned long long o = atomicMax(&T.claimA[t0], key);
   if (o > key) status = CAND_LOST;
   C[nc++] = t0;
   for (int h = 0; h < nc && status == CAND_OK; h++) {
@@ -194,8 +210,11 @@ __global__ void __launch_bounds__(128) k_cavity(TriView<D> T, const int* act, in
       if (cC == key) continue;                       // already in this region
       if (cC > key) { status = CAND_LOST; break; }   // inside a stronger region
       unsigned long long cA = *((volatile unsigned long long*)&T.claimA[u]);
+      pbytes += 16;
       bool conf = false;
       if (cA != key) {                               // cA == key: known ring simplex
+        pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
+        ptests++;
         int4 vv = T.tv[u];
         if (!verts_ok(T, vv)) { set_error(T.st, DT_E_INTERNAL, 11); status = CAND_LOST; break; }
         int vt[4] = {vv.x, vv.y, vv.z, vv.w};
@@ -207,16 +226,19 @@ __global__ void __launch_bounds__(128) k_cavity(TriView<D> T, const int* act, in
         o = atomicMax(&T.claimA[u], key);
         if (o > key) { status = CAND_LOST; break; }
         if (nc >= S.capC) { status = CAND_OVER; break; }
+        pbytes += 16 + 16 + 4;                       // claims written, links read, list entry
         C[nc++] = u;
       } else {
         if (cA != key) atomicMax(&T.claimA[u], key);
         if (nbd >= S.capB) { status = CAND_OVER; break; }
+        pbytes += 8 + 4;                             // ring claim written, list entry
         B[nbd++] = pack_nb(t, i);
       }
     }
   }
   if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
   S.meta[slot] = make_int4(nc, nbd, status, 0);
+  if (T.prof) { atomicAdd(&T.prof[0], pbytes + 16 + 16); atomicAdd(&T.prof[1], ptests); }
 }
 
 // Winners replace their region by new simplices in fresh slots.
@@ -340,7 +362,7 @@ __device__ int walk_to(const TriView<D>& T, int s, int p, int limit) {
 }
 
 template <int D>
-__global__ void k_relocate(TriView<D> T, const int* act, int nact, int* act_out, int* nact_out) {
+__global__ void k_relocate(TriView<D> T, const int* act, int nact, int* act_out, int* nact_out, unsigned next_round) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   bool keep = false;
   int p = -1;
@@ -355,7 +377,10 @@ __global__ void k_relocate(TriView<D> T, const int* act, int nact, int* act_out,
         int r = walk_to(T, s, p, 1 << 22);
         if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); r = 0; keep = false; }
         T.loc[p] = r;
+        s = r;
       }
+      // the next round's pick
+      if (keep) atomicMax(&T.claimC[s], mkkey(next_round, p));
     }
   }
   warp_append(act_out, nact_out, keep, p);
@@ -368,10 +393,21 @@ static __global__ void k_read_pred_counters(unsigned long long* calls, int* rang
   if (reset) { g_exact_calls = 0; g_range_error = 0; }
 }
 
+void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops) {
+  for (auto& k : c->kprof)
+    if (!strcmp(k.name, name)) {
+      if (ms > 0) { k.ms += ms; k.launches++; }
+      k.bytes += bytes;
+      k.flops += flops;
+      return;
+    }
+  c->kprof.push_back({name, ms > 0 ? 1 : 0, ms, bytes, flops});
+}
+
 int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool reset) {
   void* buf = pool_get(c, "predctr_eng", 64);
   if (!buf) return set_err(c, DT_E_NOMEM, "predicate counters");
-  k_read_pred_counters<<<1, 1, 0, c->stream>>>((unsigned long long*)buf, (int*)((char*)buf + 8), reset);
+  k_read_pred_counters<<<1, 1, (++c->launches, 0), c->stream>>>((unsigned long long*)buf, (int*)((char*)buf + 8), reset);
   unsigned long long h[2];
   CUDA_OK(cudaMemcpyAsync(h, buf, 16, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(cudaStreamSynchronize(c->stream));
@@ -446,10 +482,18 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     T.st = c->status;
     T.nslots = (int)total;
     T.npts = (int)npts;
+    T.prof = nullptr;
+    unsigned long long* profc = nullptr;
+    if (c->cfg.profile) {
+      profc = (unsigned long long*)pool_get(c, "eng.prof", 64);
+      if (!profc) return set_err(c, DT_E_NOMEM, "profile counters");
+      CUDA_OK(cudaMemsetAsync(profc, 0, 64, s));
+      T.prof = profc;
+    }
 
-    k_init<D><<<ceil_div(ninst, 64), 64, 0, s>>>(T, ninst, dpoff, run.toff, run.inst_status);
+    k_init<D><<<ceil_div(ninst, 64), 64, (++c->launches, 0), s>>>(T, ninst, dpoff, run.toff, run.inst_status);
     if (npts > 0)
-      k_locate_init<D><<<(unsigned)ceil_div<int64_t>(npts, 256), 256, 0, s>>>(T, npts, run.toff,
+      k_locate_init<D><<<(unsigned)ceil_div<int64_t>(npts, 256), 256, (++c->launches, 0), s>>>(T, npts, run.toff,
                                                                              run.inst_status, act0, cnt);
     int* h = c->counters_host;
     CUDA_OK(cudaMemcpyAsync(h, cnt, 4, cudaMemcpyDeviceToHost, s));
@@ -483,16 +527,31 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
       CUDA_OK(cudaMemsetAsync(cnt + 4, 0, 16, s));
       unsigned nb = (unsigned)ceil_div(nact, 256);
-      k_pick<D><<<nb, 256, 0, s>>>(T, ain, nact, round);
-      k_cavity<D><<<(unsigned)ceil_div(nact, 128), 128, 0, s>>>(T, ain, nact, round, S);
+      const bool prof = c->cfg.profile != 0;
+      if (prof) cudaEventRecord(c->pev[0], s);
+      if (round == 1) k_pick<D><<<nb, 256, (++c->launches, 0), s>>>(T, ain, nact, round);
+      if (prof) cudaEventRecord(c->pev[1], s);
+      k_cavity<D><<<(unsigned)ceil_div(nact, 128), 128, (++c->launches, 0), s>>>(T, ain, nact, round, S);
+      if (prof) cudaEventRecord(c->pev[2], s);
       unsigned ib = (unsigned)std::min<int64_t>(ceil_div<int64_t>(capCand, 128), 152 * 16);
-      k_insert<D><<<ib, 128, 0, s>>>(T, round, S);
-      k_relocate<D><<<nb, 256, 0, s>>>(T, ain, nact, aout, cnt + 5);
+      k_insert<D><<<ib, 128, (++c->launches, 0), s>>>(T, round, S);
+      if (prof) cudaEventRecord(c->pev[3], s);
+      k_relocate<D><<<nb, 256, (++c->launches, 0), s>>>(T, ain, nact, aout, cnt + 5, round + 1);
+      if (prof) cudaEventRecord(c->pev[4], s);
       CUDA_OK(cudaMemcpyAsync(h, cnt + 5, 4, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
       if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { failed = true; break; }
       if (c->status_host->error) return check_status(c, "insertion round");
+      if (prof) {
+        const char* names[4] = {D == 2 ? "k_pick<2>" : "k_pick<3>", D == 2 ? "k_cavity<2>" : "k_cavity<3>",
+                                D == 2 ? "k_insert<2>" : "k_insert<3>", D == 2 ? "k_relocate<2>" : "k_relocate<3>"};
+        for (int q = 0; q < 4; q++) {
+          float ms = 0;
+          cudaEventElapsedTime(&ms, c->pev[q], c->pev[q + 1]);
+          prof_add(c, names[q], ms, 0, 0);
+        }
+      }
       int nnew = h[0];
       if (getenv("GDT_DEBUG")) {
         int hc[4];
@@ -513,6 +572,13 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     }
     run.rounds = (int)round;
     if (failed) { grow *= 2; continue; }
+    if (profc) {
+      unsigned long long hp[2];
+      CUDA_OK(cudaMemcpyAsync(hp, profc, 16, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      // insphere filter: about 145 FP64 operations in 3D, 40 in 2D
+      prof_add(c, D == 2 ? "k_cavity<2>" : "k_cavity<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 40 : 145));
+    }
     run.h_status.assign(ninst, 0);
     run.h_tcount.assign(ninst, 0);
     CUDA_OK(cudaMemcpyAsync(run.h_status.data(), run.inst_status, 4 * ninst, cudaMemcpyDeviceToHost, s));

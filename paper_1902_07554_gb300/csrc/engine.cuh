@@ -46,6 +46,8 @@ struct TriView {
   DevStatus* st;
   int nslots;               // total simplex slots (bounds for every link)
   int npts;                 // total points (bounds for every vertex)
+  unsigned long long* prof; // profile counters (null unless profiling):
+                            // [0] bytes touched by k_cavity, [1] its conflict tests
 };
 
 struct CandScratch {

@@ -81,12 +81,12 @@ int merge(dt_ctx* c, int dim, const EngineRun& parts, const int* gid_sorted, con
   if (!table || !cnt || !all) return set_err(c, DT_E_NOMEM, "merge buffers");
   CUDA_OK(cudaMemsetAsync(table, 0xff, 4 * (size_t)tsize, s));
   CUDA_OK(cudaMemsetAsync(cnt, 0, 16, s));
-  if (nb) k_hash_insert<<<(unsigned)ceil_div<int64_t>(nb, 256), 256, 0, s>>>(brows, nb, table, tsize - 1, cnt + 1);
+  if (nb) k_hash_insert<<<(unsigned)ceil_div<int64_t>(nb, 256), 256, (++c->launches, 0), s>>>(brows, nb, table, tsize - 1, cnt + 1);
   if (nt) CUDA_OK(cudaMemcpyAsync(all, trows, 16 * (size_t)nt, cudaMemcpyDeviceToDevice, s));
   if (ntb) {
     unsigned g = (unsigned)ceil_div<int64_t>(ntb, 256);
-    if (dim == 2) k_merge_select<2><<<g, 256, 0, s>>>(tbrows, ntb, label_by_gid, brows, table, tsize - 1, all + nt, cnt);
-    else k_merge_select<3><<<g, 256, 0, s>>>(tbrows, ntb, label_by_gid, brows, table, tsize - 1, all + nt, cnt);
+    if (dim == 2) k_merge_select<2><<<g, 256, (++c->launches, 0), s>>>(tbrows, ntb, label_by_gid, brows, table, tsize - 1, all + nt, cnt);
+    else k_merge_select<3><<<g, 256, (++c->launches, 0), s>>>(tbrows, ntb, label_by_gid, brows, table, tsize - 1, all + nt, cnt);
   }
   int h[2];
   CUDA_OK(cudaMemcpyAsync(h, cnt, 8, cudaMemcpyDeviceToHost, s));

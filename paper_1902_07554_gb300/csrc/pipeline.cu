@@ -19,7 +19,7 @@ static int run_direct(dt_ctx* c, const void* P, int64_t n, int dim) {
   int* pinst = (int*)pool_get(c, "pl.pinst", 4 * n);
   if (!gid || !pinst) return set_err(c, DT_E_NOMEM, "pipeline buffers");
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
-  k_iota<<<g, 256, 0, s>>>(gid, n, 0);
+  k_iota<<<g, 256, (++c->launches, 0), s>>>(gid, n, 0);
   CUDA_OK(cudaMemsetAsync(pinst, 0, 4 * n, s));
   std::vector<int64_t> poff = {0, n};
   int rc = engine_run(c, c->run_parts, dim, P, gid, pinst, n, poff, "parts");
@@ -67,11 +67,11 @@ static int compact_flags(dt_ctx* c, const unsigned char* flag, int64_t n, int* o
   int* pos = (int*)pool_get(c, std::string(tag) + ".p", 4 * std::max<int64_t>(n, 1));
   if (!f32 || !pos) return set_err(c, DT_E_NOMEM, "compaction");
   unsigned g = (unsigned)ceil_div<int64_t>(std::max<int64_t>(n, 1), 256);
-  k_u8_to_i32<<<g, 256, 0, c->stream>>>(flag, n, f32);
+  k_u8_to_i32<<<g, 256, (++c->launches, 0), c->stream>>>(flag, n, f32);
   int total = 0;
   int rc = exclusive_scan_i32(c, f32, pos, n, &total);
   if (rc) return rc;
-  k_flag_compact<<<g, 256, 0, c->stream>>>(flag, pos, n, out);
+  k_flag_compact<<<g, 256, (++c->launches, 0), c->stream>>>(flag, pos, n, out);
   *m = total;
   return 0;
 }
@@ -176,7 +176,7 @@ static int run_dc(dt_ctx* c, const void* P, int64_t n, int dim, int k, double fr
   if (!PB || !gidB || !zB) return set_err(c, DT_E_NOMEM, "border points");
   if (nVB) {
     gather_points(c, dim, Ps, idxB, nVB, PB);
-    k_gather_i32<<<(unsigned)ceil_div<int64_t>(nVB, 256), 256, 0, s>>>(gid_sorted, idxB, nVB, gidB);
+    k_gather_i32<<<(unsigned)ceil_div<int64_t>(nVB, 256), 256, (++c->launches, 0), s>>>(gid_sorted, idxB, nVB, gidB);
     CUDA_OK(cudaMemsetAsync(zB, 0, 4 * nVB, s));
   }
   rc = engine_run(c, c->run_border, dim, PB, gidB, zB, nVB, {0, nVB}, "border");
@@ -202,7 +202,7 @@ static int run_dc(dt_ctx* c, const void* P, int64_t n, int dim, int k, double fr
   c->border_vtx = (int32_t*)pool_get(c, "dc.bv", 4 * std::max<int64_t>(nVB, 1));
   if (!fg || !c->border_vtx) return set_err(c, DT_E_NOMEM, "border vertex list");
   CUDA_OK(cudaMemsetAsync(fg, 0, n, s));
-  k_flag_by_gid<<<(unsigned)ceil_div<int64_t>(n, 256), 256, 0, s>>>(vflag, gid_sorted, n, fg);
+  k_flag_by_gid<<<(unsigned)ceil_div<int64_t>(n, 256), 256, (++c->launches, 0), s>>>(vflag, gid_sorted, n, fg);
   int64_t nbv = 0;
   rc = compact_flags(c, fg, n, c->border_vtx, &nbv, "dc.cbv");
   if (rc) return rc;
@@ -264,7 +264,7 @@ extern "C" int dt_label_points(dt_ctx* c, const double* P, int64_t n, int dim, c
   int* zeros = (int*)pool_get(c, "lp.z", 4 * m);
   int* lab = (int*)pool_get(c, "lp.out", 4 * n);
   if (!r32 || !zeros || !lab) return set_err(c, DT_E_NOMEM, "label buffers");
-  k_i64_to_i32b<<<(unsigned)ceil_div<int64_t>(m, 256), 256, 0, s>>>(r64, r32, m);
+  k_i64_to_i32b<<<(unsigned)ceil_div<int64_t>(m, 256), 256, (++c->launches, 0), s>>>(r64, r32, m);
   CUDA_OK(cudaMemsetAsync(zeros, 0, 4 * m, s));
   EngineRun run;
   rc = engine_run(c, run, dim, dS, r32, zeros, m, {0, m}, "lp.dt");

@@ -116,10 +116,10 @@ int radix_sort_pairs(dt_ctx* c, K* keys, V* vals, int64_t n, int bits, const std
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; p++) {
     int shift = p * 8;
-    k_rs_hist<K><<<ntiles, RS_T, 0, s>>>(ka, n, shift, hist, ntiles);
+    k_rs_hist<K><<<ntiles, RS_T, (++c->launches, 0), s>>>(ka, n, shift, hist, ntiles);
     int rc = exclusive_scan_i32(c, hist, offs, (int64_t)256 * ntiles, nullptr);
     if (rc) return rc;
-    k_rs_scatter<K, V><<<ntiles, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, offs, ntiles);
+    k_rs_scatter<K, V><<<ntiles, RS_T, (++c->launches, 0), s>>>(ka, va, kb, vb, n, shift, offs, ntiles);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
@@ -143,10 +143,10 @@ int group_rank(dt_ctx* c, const int* g, int64_t n, int* rank, int* sizes, int ng
   int* hist = (int*)pool_get(c, "gr.hist", 4 * (size_t)256 * ntiles + 4);
   int* offs = (int*)pool_get(c, "gr.offs", 4 * (size_t)256 * ntiles + 4);
   if (!hist || !offs) return set_err(c, DT_E_NOMEM, "group rank buffers");
-  k_grp_hist<<<ntiles, RS_T, 0, s>>>(g, n, hist, ntiles);
+  k_grp_hist<<<ntiles, RS_T, (++c->launches, 0), s>>>(g, n, hist, ntiles);
   int rc = exclusive_scan_i32(c, hist, offs, (int64_t)256 * ntiles, nullptr);
   if (rc) return rc;
-  k_grp_rank<<<ntiles, RS_T, 0, s>>>(g, n, offs, ntiles, rank);
+  k_grp_rank<<<ntiles, RS_T, (++c->launches, 0), s>>>(g, n, offs, ntiles, rank);
   if (sizes) {
     // size of group d = offs[(d+1)*ntiles] - offs[d*ntiles]; the last needs the total
     rc = group_sizes_from_offsets(c, hist, offs, ntiles, sizes, ngroups);
@@ -165,7 +165,7 @@ __global__ void k_grp_sizes(const int* hist, int ntiles, int* sizes, int ngroups
 
 int group_sizes_from_offsets(dt_ctx* c, const int* hist, const int* offs, int ntiles, int* sizes, int ngroups) {
   (void)offs;
-  k_grp_sizes<<<ceil_div(ngroups, 128), 128, 0, c->stream>>>(hist, ntiles, sizes, ngroups);
+  k_grp_sizes<<<ceil_div(ngroups, 128), 128, (++c->launches, 0), c->stream>>>(hist, ntiles, sizes, ngroups);
   return 0;
 }
 

@@ -105,16 +105,16 @@ template <typename T>
 static int scan_rec(dt_ctx* c, const T* in, T* out, int64_t n, int depth) {
   int64_t nb = ceil_div<int64_t>(n, SCAN_TILE);
   if (nb == 1) {
-    k_scan_tiles<T><<<1, SCAN_T, 0, c->stream>>>(in, out, (T*)nullptr, n);
+    k_scan_tiles<T><<<1, SCAN_T, (++c->launches, 0), c->stream>>>(in, out, (T*)nullptr, n);
     return 0;
   }
   T* sums = (T*)pool_get(c, "scan.s" + std::to_string(depth), sizeof(T) * nb);
   T* soff = (T*)pool_get(c, "scan.o" + std::to_string(depth), sizeof(T) * nb);
   if (!sums || !soff) return set_err(c, DT_E_NOMEM, "scan");
-  k_scan_tiles<T><<<(unsigned)nb, SCAN_T, 0, c->stream>>>(in, out, sums, n);
+  k_scan_tiles<T><<<(unsigned)nb, SCAN_T, (++c->launches, 0), c->stream>>>(in, out, sums, n);
   int rc = scan_rec<T>(c, sums, soff, nb, depth + 1);
   if (rc) return rc;
-  k_scan_add<T><<<(unsigned)nb, SCAN_T, 0, c->stream>>>(out, soff, n);
+  k_scan_add<T><<<(unsigned)nb, SCAN_T, (++c->launches, 0), c->stream>>>(out, soff, n);
   return 0;
 }
 
