@@ -207,6 +207,31 @@ DT_API int dt_partition_graph(dt_ctx* ctx, const double* S, int64_t eta, int dim
                        const int64_t* w, int64_t m, int k, double eps, int rounds,
                        int32_t* out);
 
+/* ---- allocation-free variant ---- */
+
+/* Sample selection (the eta smallest keys splitmix64(splitmix64(seed) ^ i),
+ * i < n; the same indices dt_triangulate draws for its sample) for callers
+ * that cannot allocate device memory: code running inside an allocator or a
+ * memory pool it does not own, processes with capped or audited allocations,
+ * or real-time paths where cudaMalloc and its implicit synchronisation are
+ * not allowed.  The paper has no counterpart; it is a systems entry point.
+ *
+ * Needs no context and allocates nothing: its scratch is one file-scope
+ * device array of 9240 bytes that every GPU loading this library keeps until
+ * the process exits.  out_ids: eta int32 in DEVICE memory of `device`
+ * (caller-allocated; host pointers are rejected), written in ascending order.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream); the call
+ * synchronises it before returning.
+ * Limits: 1 <= eta <= n <= 2^31 - 1; anything else returns DT_E_ARG.
+ * The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it: make that
+ * first call before any stream capture.  All calls share the array, which
+ * keeps the last call's contents (each call clears what must start at zero);
+ * calls that overlap on the GPU race on it and must be ordered by the caller.
+ * Returns DT_OK, DT_E_ARG or DT_E_CUDA. */
+DT_API int dt_select_sample_noalloc(int device, void* cuda_stream, int64_t n, int64_t eta, uint64_t seed,
+                                    int32_t* out_ids);
+
 #ifdef __cplusplus
 }
 #endif

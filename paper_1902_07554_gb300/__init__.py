@@ -112,6 +112,7 @@ def load_library(build: bool = True):
         "dt_label_points": ([p, p, i64, i32, p, p, p, i64, p], i32),
         "dt_partition_graph": ([p, p, i64, i32, p, p, i64, i32, dbl, i32, p], i32),
         "dt_get_kernel_profile": ([p, p, i32, p], i32),
+        "dt_select_sample_noalloc": ([i32, p, i64, i64, ctypes.c_uint64, p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
