@@ -47,6 +47,21 @@ WORKLOADS = {
 }
 
 
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job Mpoints/s: all ranks' points over the slowest rank's step time."""
+    return world * n_per_rank / (ms_max / 1e3) / 1e6
+
+
 def gen_points(w, seed_offset=0):
     if w["gen"] == "uniform":
         return pointsets.uniform(w["n"], w["dim"], w["seed"] + seed_offset)
@@ -228,11 +243,8 @@ def main():
     if dist:
         dist.barrier()
     ms = sum(step_ms) / len(step_ms)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * n / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
+    value = job_value(n, world, ms_max)
     stats = tri.stats().as_dict()
     tri.configure(profile=0)
 
@@ -250,10 +262,7 @@ def main():
         tri.simplices(out=out_pin[:cnt])
         e2e_ms.append(1e3 * (time.perf_counter() - t))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
-    e2e_t = torch.tensor([e2e_step], dtype=torch.float64, device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * n / (float(e2e_t.item()) / 1e3) / 1e6, "unit": "Mpoints/s",
+    e2e = {"value": job_value(n, world, max_over_ranks(e2e_step, dist, f"cuda:{local}")), "unit": "Mpoints/s",
            "h2d_bytes_per_step": int(n * w["dim"] * 8), "d2h_bytes_per_step": int(cnt * (w["dim"] + 1) * 4),
            "ms_per_step": e2e_step}
 
