@@ -182,6 +182,31 @@ DT_API const char* dt_last_error(dt_ctx* ctx);
 /* Release the context and every buffer it owns.  NULL is ignored. */
 DT_API void dt_destroy(dt_ctx* ctx);
 
+/* ---- batched form: many independent problems in one call ---- */
+
+/* Triangulate `count` independent point sets of dimension dim in one engine
+ * run (one set of kernel launches for all of them).  Instance i is rows
+ * offsets[i] .. offsets[i+1]-1 of points (host or device, float64 row-major);
+ * offsets: count+1 int64 in HOST memory, offsets[0] = 0, non-decreasing,
+ * total below 2^28.  Each instance is triangulated directly (Alg. 1 base
+ * case); perturbation ranks are the point order inside each instance.
+ * Duplicates are checked inside each instance (DT_E_DUPLICATE); an instance
+ * that is flat or has fewer than dim+1 points gets an empty result and a
+ * per-instance status (dt_get_batch_status).  Replaces the previous result. */
+DT_API int dt_triangulate_batch(dt_ctx* ctx, const double* points, const int64_t* offsets, int count, int dim);
+
+/* Simplices of the last batch: rows of dim+1 int32 INSTANCE-LOCAL vertex
+ * indices (each row sorted, rows sorted per instance, instances in order)
+ * into out (host or device, capacity rows); out_offsets (host, count+1, may
+ * be NULL) receives each instance's first row; *total the row count.  With
+ * out == NULL only the counts are written. */
+DT_API int dt_get_batch_simplices(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t* out_offsets,
+                                  int64_t* total);
+
+/* Per-instance status of the last batch: 0, DT_E_DEGENERATE (flat) or
+ * DT_E_ARG (fewer than dim+1 points); status: count int32 (host). */
+DT_API int dt_get_batch_status(dt_ctx* ctx, int32_t* status, int count);
+
 /* ---- step-level entry points (operate on caller buffers; host or device) ---- */
 
 /* Exact predicate signs for m index tuples into points (n x dim, host or

@@ -112,6 +112,9 @@ def load_library(build: bool = True):
         "dt_label_points": ([p, p, i64, i32, p, p, p, i64, p], i32),
         "dt_partition_graph": ([p, p, i64, i32, p, p, i64, i32, dbl, i32, p], i32),
         "dt_get_kernel_profile": ([p, p, i32, p], i32),
+        "dt_triangulate_batch": ([p, p, p, i32, i32], i32),
+        "dt_get_batch_simplices": ([p, p, i64, p, p], i32),
+        "dt_get_batch_status": ([p, p, i32], i32),
         "dt_select_sample_noalloc": ([i32, p, i64, i64, ctypes.c_uint64, p], i32),
     }
     for name, (args, res) in sig.items():
@@ -198,6 +201,36 @@ class Triangulator:
         P, n, dim = _as_points(points)
         self._check(self.L.dt_triangulate(self.ctx, _ptr(P), n, dim, k, float(sample_frac)))
         return self.simplices() if fetch else None
+
+    def triangulate_batch(self, points, offsets, fetch: bool = True):
+        """Independent DTs of points[offsets[i]:offsets[i+1]]; returns a list of
+        (m_i, dim+1) int32 arrays of instance-local indices (or None)."""
+        P, n, dim = _as_points(points)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._last_batch = len(off) - 1
+        self._check(self.L.dt_triangulate_batch(self.ctx, _ptr(P), _ptr(off), len(off) - 1, dim))
+        return self.batch_simplices() if fetch else None
+
+    def batch_simplices(self):
+        total = ctypes.c_int64()
+        cnt = self.stats()
+        nb = self._batch_count()
+        ro = np.empty(nb + 1, dtype=np.int64)
+        self._check(self.L.dt_get_batch_simplices(self.ctx, None, 0, _ptr(ro), ctypes.byref(total)))
+        out = np.empty((total.value, cnt.dim + 1), dtype=np.int32)
+        self._check(self.L.dt_get_batch_simplices(self.ctx, _ptr(out), total.value, _ptr(ro), ctypes.byref(total)))
+        return [out[ro[i]:ro[i + 1]] for i in range(nb)]
+
+    def _batch_count(self):
+        # probe the last batch's instance count through the status call
+        for guess in (self._last_batch,) if getattr(self, "_last_batch", None) else ():
+            return guess
+        raise RuntimeError("no batch")
+
+    def batch_status(self, count):
+        out = np.empty(count, dtype=np.int32)
+        self._check(self.L.dt_get_batch_status(self.ctx, _ptr(out), count))
+        return out
 
     def simplices(self, out=None):
         cnt = ctypes.c_int64()

@@ -149,23 +149,29 @@ __global__ void k_iota(int* a, int64_t n, int start) {
 // Exact-duplicate detection with an open-addressing table of point indices
 // keyed by the coordinate bits (-0.0 folded onto +0.0).
 template <int D>
-__global__ void k_dup_check(const typename PT<D>::T* P, int64_t n, int* table, unsigned mask, int* dup) {
+__global__ void k_dup_check(const typename PT<D>::T* P, int64_t n, int* table, unsigned mask, int* dup,
+                            const int* inst) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = cx(P[i]) + 0.0, y = cy(P[i]) + 0.0, z = cz(P[i]) + 0.0;
+  int my = inst ? inst[i] : 0;
   uint64_t h = splitmix64((uint64_t)__double_as_longlong(x) ^ splitmix64((uint64_t)__double_as_longlong(y) ^
-                          splitmix64((uint64_t)__double_as_longlong(z))));
+                          splitmix64((uint64_t)__double_as_longlong(z) ^ (uint64_t)my)));
   unsigned slot = (unsigned)h & mask;
   for (unsigned probe = 0; probe <= mask; probe++) {
     int prev = atomicCAS(&table[slot], -1, (int)i);
     if (prev == -1) return;
-    if (cx(P[prev]) == x && cy(P[prev]) == y && cz(P[prev]) == z) { atomicExch(dup, 1); return; }
+    if (cx(P[prev]) == x && cy(P[prev]) == y && cz(P[prev]) == z && (!inst || inst[prev] == my)) {
+      atomicExch(dup, 1);
+      return;
+    }
     slot = (slot + 1) & mask;
   }
   atomicExch(dup, 2);
 }
 
-int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out, const char* tag) {
+int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out, const char* tag,
+                 const int* inst) {
   int rc = 0;
   std::string t(tag);
   const double* src = (const double*)stage_in(c, points, sizeof(double) * n * dim, t + ".raw", &rc);
@@ -182,10 +188,10 @@ int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_o
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
   if (dim == 2) {
     k_pack_points<2><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double2*)P, flags);
-    k_dup_check<2><<<g, 256, (++c->launches, 0), c->stream>>>((const double2*)P, n, table, tsize - 1, flags + 1);
+    k_dup_check<2><<<g, 256, (++c->launches, 0), c->stream>>>((const double2*)P, n, table, tsize - 1, flags + 1, inst);
   } else {
     k_pack_points<3><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double4_32a*)P, flags);
-    k_dup_check<3><<<g, 256, (++c->launches, 0), c->stream>>>((const double4_32a*)P, n, table, tsize - 1, flags + 1);
+    k_dup_check<3><<<g, 256, (++c->launches, 0), c->stream>>>((const double4_32a*)P, n, table, tsize - 1, flags + 1, inst);
   }
   int h[2];
   CUDA_OK(cudaMemcpyAsync(h, flags, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -217,6 +223,7 @@ extern "C" int dt_triangulate(dt_ctx* c, const double* points, int64_t n, int di
   c->stats.dim = dim;
   c->stats.k = 1;
   c->kprof.clear();
+  c->batch_count = 0;
   long long l0 = c->launches;
   cudaEventRecord(c->ev[0], c->stream);
   int rc = run_pipeline(c, points, n, dim, k, sample_frac);
@@ -248,6 +255,64 @@ extern "C" int dt_get_kernel_profile(dt_ctx* c, dt_kernel_profile* out, int max,
     out[i].bytes = c->kprof[i].bytes;
     out[i].flops = c->kprof[i].flops;
   }
+  return DT_OK;
+}
+
+extern "C" int dt_triangulate_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count, int dim) {
+  if (!c) return DT_E_ARG;
+  c->err.clear();
+  if (!points || !offsets || count < 1 || (dim != 2 && dim != 3))
+    return set_err(c, DT_E_ARG, "batch: points, offsets, count >= 1 and dim 2 or 3 required");
+  if (offsets[0] != 0) return set_err(c, DT_E_ARG, "batch: offsets[0] must be 0");
+  for (int i = 0; i < count; i++)
+    if (offsets[i + 1] < offsets[i]) return set_err(c, DT_E_ARG, "batch: offsets must be non-decreasing");
+  if (offsets[count] >= (int64_t(1) << 28)) return set_err(c, DT_E_ARG, "batch: total points must be below 2^28");
+  if (cudaSetDevice(c->device) != cudaSuccess) { cudaGetLastError(); return set_err(c, DT_E_CUDA, "cudaSetDevice"); }
+  c->dim = dim;
+  c->n = offsets[count];
+  c->nout = 0;
+  c->out = nullptr;
+  c->batch_count = 0;
+  memset(&c->stats, 0, sizeof(c->stats));
+  c->stats.n = c->n;
+  c->stats.dim = dim;
+  c->stats.k = 1;
+  c->kprof.clear();
+  long long l0 = c->launches;
+  cudaEventRecord(c->ev[0], c->stream);
+  int rc = run_batch(c, points, offsets, count, dim);
+  if (rc) return rc;
+  cudaEventRecord(c->ev[1], c->stream);
+  cudaError_t e = cudaEventSynchronize(c->ev[1]);
+  if (e != cudaSuccess) return set_err(c, gdt_cuda_fail(e, "sync", __FILE__, __LINE__), "final sync");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+  c->stats.ms_total = ms;
+  unsigned long long calls; int range;
+  rc = pred_counters_engine(c, &calls, &range, true);
+  if (rc) return rc;
+  c->stats.exact_calls = (int32_t)std::min<unsigned long long>(calls, 0x7fffffffull);
+  c->stats.simplices = c->nout;
+  c->stats.launches = c->launches - l0;
+  return DT_OK;
+}
+
+extern "C" int dt_get_batch_simplices(dt_ctx* c, int32_t* out, int64_t capacity, int64_t* out_offsets,
+                                      int64_t* total) {
+  if (!c || !total) return DT_E_ARG;
+  if (!c->batch_count) return set_err(c, DT_E_ARG, "no batch result");
+  *total = c->nout;
+  if (out_offsets)
+    for (int i = 0; i <= c->batch_count; i++) out_offsets[i] = c->batch_offsets[i];
+  if (!out) return DT_OK;
+  if (capacity < c->nout) return set_err(c, DT_E_ARG, "capacity too small");
+  return copy_out(c, out, c->out, sizeof(int32_t) * (c->dim + 1) * c->nout);
+}
+
+extern "C" int dt_get_batch_status(dt_ctx* c, int32_t* status, int count) {
+  if (!c || !status) return DT_E_ARG;
+  if (count != c->batch_count) return set_err(c, DT_E_ARG, "count differs from the last batch");
+  for (int i = 0; i < count; i++) status[i] = c->batch_status[i];
   return DT_OK;
 }
 

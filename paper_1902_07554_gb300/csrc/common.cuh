@@ -25,6 +25,7 @@ struct DevStatus {
   int overflow_cav;   // a candidate's cavity exceeded its scratch capacity
   int pad;
   unsigned long long exact_calls;   // exact-arithmetic fallbacks taken
+  int dbg[16];        // diagnostics of the first internal error
 };
 
 __device__ __forceinline__ void set_error(DevStatus* st, int code, int detail) {

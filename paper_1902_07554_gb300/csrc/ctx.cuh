@@ -40,6 +40,10 @@ struct dt_ctx {
   int32_t* border_vtx = nullptr;         // |V_B| global ids, ascending
   int64_t n_border = 0;
   gdt::EngineRun run_sample, run_parts, run_border;
+  // batched call: per-instance row offsets (count+1) and status
+  std::vector<int64_t> batch_offsets;
+  std::vector<int> batch_status;
+  int batch_count = 0;
 };
 
 namespace gdt {

@@ -171,81 +171,145 @@ __global__ void k_pick(TriView<D> T, const int* act, int nact, unsigned round) {
 
 enum { CAND_OK = 0, CAND_LOST = 1, CAND_OVER = 2 };
 
+// Nominees of a round: the point holding the strongest key of its simplex
+// (left in claimC by the pick), unless a neighbour of that simplex holds a
+// stronger key -- every neighbour lies in the nominee's region or ring, and a
+// stronger key there belongs to a nominee whose region contains it, so the
+// weaker one would lose anyway.  Nominees go to a dense list.
 template <int D>
-__global__ void __launch_bounds__(128) k_cavity(TriView<D> T, const int* act, int nact, unsigned round,
-                                                CandScratch S) {
+__global__ void k_nominate(TriView<D> T, const int* act, const int* nact_p, unsigned round, int* nom, int* nnom) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nact) return;
-  int p = act[idx];
-  unsigned long long key = mkkey(round, p);
-  int t0 = T.loc[p];
-  // the pick left, in claimC, the strongest key of the points in each simplex
-  if (*((volatile unsigned long long*)&T.claimC[t0]) != key) return;   // not its simplex's nominee
-  // Every neighbour of t0 lies in p's region or ring; a stronger nominee in a
-  // neighbour has that neighbour in its own region, so p would lose: skip.
-  {
-    int4 nn0 = T.tn[t0];
-    for (int i = 0; i <= D; i++) {
-      int u = nb_simplex(get4(nn0, i));
-      if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) return;
-    }
-  }
-  int slot = atomicAdd(S.count, 1);
-  if (slot >= S.cap) return;
-  S.cand[slot] = p;
-  int* C = S.cav + (int64_t)slot * S.capC;
-  int* B = S.bnd + (int64_t)slot * S.capB;
-  int nc = 0, nbd = 0, status = CAND_OK;
-  unsigned long long pbytes = sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1), ptests = 0;
-  unsigned long long o = atomicMax(&T.claimA[t0], key);
-  if (o > key) status = CAND_LOST;
-  C[nc++] = t0;
-  for (int h = 0; h < nc && status == CAND_OK; h++) {
-    int t = C[h];
-    int4 nn = T.tn[t];
-    for (int i = 0; i <= D; i++) {
-      int u = nb_simplex(get4(nn, i));
-      if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 10); status = CAND_LOST; break; }
-      unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
-      if (cC == key) continue;                       // already in this region
-      if (cC > key) { status = CAND_LOST; break; }   // inside a stronger region
-      unsigned long long cA = *((volatile unsigned long long*)&T.claimA[u]);
-      pbytes += 16;
-      bool conf = false;
-      if (cA != key) {                               // cA == key: known ring simplex
-        pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
-        ptests++;
-        int4 vv = T.tv[u];
-        if (!verts_ok(T, vv)) { set_error(T.st, DT_E_INTERNAL, 11); status = CAND_LOST; break; }
-        int vt[4] = {vv.x, vv.y, vv.z, vv.w};
-        conf = in_conflict(T.pts, T.gid, vt, p);
-      }
-      if (conf) {
-        o = atomicMax(&T.claimC[u], key);
-        if (o > key) { status = CAND_LOST; break; }
-        o = atomicMax(&T.claimA[u], key);
-        if (o > key) { status = CAND_LOST; break; }
-        if (nc >= S.capC) { status = CAND_OVER; break; }
-        pbytes += 16 + 16 + 4;                       // claims written, links read, list entry
-        C[nc++] = u;
-      } else {
-        if (cA != key) atomicMax(&T.claimA[u], key);
-        if (nbd >= S.capB) { status = CAND_OVER; break; }
-        pbytes += 8 + 4;                             // ring claim written, list entry
-        B[nbd++] = pack_nb(t, i);
+  int nact = *nact_p;
+  bool take = false;
+  int p = -1;
+  if (idx < nact) {
+    p = act[idx];
+    unsigned long long key = mkkey(round, p);
+    int t0 = T.loc[p];
+    if (*((volatile unsigned long long*)&T.claimC[t0]) == key) {
+      take = true;
+      int4 nn0 = T.tn[t0];
+      for (int i = 0; i <= D; i++) {
+        int u = nb_simplex(get4(nn0, i));
+        if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) take = false;
       }
     }
   }
-  if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
-  S.meta[slot] = make_int4(nc, nbd, status, 0);
-  if (T.prof) { atomicAdd(&T.prof[0], pbytes + 16 + 16); atomicAdd(&T.prof[1], ptests); }
+  warp_append(nom, nnom, take, p);
 }
 
-// Winners replace their region by new simplices in fresh slots.
+// One warp per nominee grows its conflict region: each lane inspects one
+// (region simplex, facet) pair per step, up to 32/(D+1) region simplices per
+// step.  Conflicting neighbours join the region (claimC/claimA atomicMax; the
+// returned old value also deduplicates lanes that reach the same simplex),
+// the others become boundary facets (ring claim in claimA).
 template <int D>
-__global__ void __launch_bounds__(128) k_insert(TriView<D> T, unsigned round, CandScratch S) {
-  int total = min(*S.count, S.cap);
-  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < total; slot += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(128) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
+                                                  CandScratch S) {
+  const unsigned FULL = 0xffffffffu;
+  int lane = threadIdx.x & 31;
+  int nwarp = (gridDim.x * blockDim.x) >> 5;
+  int nnom = min(*nnom_p, S.cap);
+  constexpr int PER = 32 / (D + 1);
+  for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < nnom; slot += nwarp) {
+    int p = nom[slot];
+    unsigned long long key = mkkey(round, p);
+    int* C = S.cav + (int64_t)slot * S.capC;
+    int* B = S.bnd + (int64_t)slot * S.capB;
+    int t0 = T.loc[p];
+    int status = CAND_OK;
+    unsigned long long pbytes = 0, ptests = 0;
+    if (lane == 0) {
+      S.cand[slot] = p;
+      unsigned long long o = atomicMax(&T.claimA[t0], key);
+      if (o > key) status = CAND_LOST;
+      C[0] = t0;
+      pbytes += sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1) + 16 + 4;
+    }
+    status = __shfl_sync(FULL, status, 0);
+    int nc = 1, nbd = 0;
+    __syncwarp();
+    for (int h = 0; h < nc && status == CAND_OK;) {
+      const int nc0 = nc;                                // region simplices known at this step
+      int j = h + lane / (D + 1), i = lane % (D + 1);
+      bool valid = lane < PER * (D + 1) && j < nc0;
+      bool addC = false, addB = false, lost = false, bad = false;
+      int t = -1, u = -1;
+      if (valid) {
+        t = C[j];
+        u = nb_simplex(*comp_ptr(T.tn, t, i));
+        if (!slot_ok(T, u)) {
+          bad = true;
+        } else {
+          unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
+          pbytes += 16;
+          if (cC > key) {
+            lost = true;                                 // inside a stronger region
+          } else if (cC != key) {
+            int4 vv = T.tv[u];
+            pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
+            ptests++;
+            if (!verts_ok(T, vv)) {
+              bad = true;
+            } else {
+              int vt[4] = {vv.x, vv.y, vv.z, vv.w};
+              if (in_conflict(T.pts, T.gid, vt, p)) {
+                unsigned long long o = atomicMax(&T.claimC[u], key);
+                if (o > key) {
+                  lost = true;
+                } else if (o < key) {                    // first lane to claim it
+                  unsigned long long o2 = atomicMax(&T.claimA[u], key);
+                  if (o2 > key) lost = true; else addC = true;
+                  pbytes += 16 + 16 + 4;
+                }
+              } else {
+                atomicMax(&T.claimA[u], key);
+                addB = true;
+                pbytes += 8 + 4;
+              }
+            }
+          }
+        }
+      }
+      if (bad) set_error(T.st, DT_E_INTERNAL, 10);
+      if (__any_sync(FULL, lost || bad)) { status = CAND_LOST; break; }
+      unsigned mC = __ballot_sync(FULL, addC), mB = __ballot_sync(FULL, addB);
+      int nC = __popc(mC), nB = __popc(mB);
+      if (nc + nC > S.capC || nbd + nB > S.capB) { status = CAND_OVER; break; }
+      unsigned lt = (1u << lane) - 1;
+      if (addC) C[nc + __popc(mC & lt)] = u;
+      if (addB) B[nbd + __popc(mB & lt)] = pack_nb(t, i);
+      nc += nC;
+      nbd += nB;
+      h = min(h + PER, nc0);                             // simplices appended now come next
+      __syncwarp();
+    }
+    if (T.prof) {
+      for (int off = 16; off; off >>= 1) {
+        pbytes += __shfl_down_sync(FULL, pbytes, off);
+        ptests += __shfl_down_sync(FULL, ptests, off);
+      }
+    }
+    if (lane == 0) {
+      if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
+      S.meta[slot] = make_int4(nc, nbd, status, 0);
+      if (T.prof) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
+    }
+    __syncwarp();
+  }
+}
+
+// One warp per nominee: a nominee wins if no stronger nominee claimed any of
+// its region (claimA) or has any of its ring in its own region (claimC).
+// Winners replace their region by the star of new simplices in fresh slots.
+template <int D>
+__global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, CandScratch S, const int* nnom_p,
+                                                  int* nwin) {
+  const unsigned FULL = 0xffffffffu;
+  int lane = threadIdx.x & 31;
+  int nwarp = (gridDim.x * blockDim.x) >> 5;
+  int total = min(*nnom_p, S.cap);
+  for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nwarp) {
     int4 m = S.meta[slot];
     if (m.z != CAND_OK) continue;
     int p = S.cand[slot];
@@ -254,28 +318,36 @@ __global__ void __launch_bounds__(128) k_insert(TriView<D> T, unsigned round, Ca
     const int* B = S.bnd + (int64_t)slot * S.capB;
     int* OUT = S.outer + (int64_t)slot * S.capB;
     int nc = m.x, nbd = m.y;
-    bool win = true;
-    for (int h = 0; h < nc && win; h++)
-      if (*((volatile unsigned long long*)&T.claimA[C[h]]) != key) win = false;
-    for (int b = 0; b < nbd && win; b++) {
+    bool ok = true;
+    for (int j = lane; j < nc; j += 32)
+      if (*((volatile unsigned long long*)&T.claimA[C[j]]) != key) ok = false;
+    // a region shared with a stronger winner may already carry its tags: stop here
+    if (!__all_sync(FULL, ok)) continue;
+    for (int b = lane; b < nbd; b += 32) {
       int t = nb_simplex(B[b]), i = nb_face(B[b]);
       int u = nb_simplex(*comp_ptr(T.tn, t, i));
-      if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 12); win = false; break; }
-      if (*((volatile unsigned long long*)&T.claimC[u]) > key) win = false;
+      if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 12); ok = false; }
+      else if (*((volatile unsigned long long*)&T.claimC[u]) > key) ok = false;
     }
-    if (!win) continue;
+    if (!__all_sync(FULL, ok)) continue;
     int inst = T.pinst[p];
-    int base = atomicAdd(&T.tcount[inst], nbd);
-    if (base + nbd > T.tend[inst]) { set_error(T.st, DT_E_OVERFLOW, 1); continue; }
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&T.tcount[inst], nbd);
+    base = __shfl_sync(FULL, base, 0);
+    if (base + nbd > T.tend[inst]) {
+      if (lane == 0) set_error(T.st, DT_E_OVERFLOW, 1);
+      continue;
+    }
     // phase 1: remember the outside links, tag boundary facets with their new simplex
-    for (int b = 0; b < nbd; b++) {
+    for (int b = lane; b < nbd; b += 32) {
       int t = nb_simplex(B[b]), i = nb_face(B[b]);
       int* cp = comp_ptr(T.tn, t, i);
       OUT[b] = *cp;
       *cp = TAGBIT | (base + b);
     }
+    __syncwarp();
     // phase 2: build the star of p over the boundary
-    for (int b = 0; b < nbd; b++) {
+    for (int b = lane; b < nbd; b += 32) {
       int t = nb_simplex(B[b]), i = nb_face(B[b]);
       int4 vv = T.tv[t];
       set4(vv, i, p);
@@ -303,21 +375,33 @@ __global__ void __launch_bounds__(128) k_insert(TriView<D> T, unsigned round, Ca
           cur = nxt;
           if (as < 0) break;
         }
-        if (link < 0) { set_error(T.st, DT_E_INTERNAL, 2); link = 0; }
+        if (link < 0) {
+          if (atomicCAS(&T.st->error, 0, DT_E_INTERNAL) == 0) {
+            T.st->detail = 2;
+            int* d = T.st->dbg;
+            d[0] = (int)round; d[1] = p; d[2] = nc; d[3] = nbd; d[4] = b; d[5] = j; d[6] = t; d[7] = i;
+            d[8] = cur; d[9] = as; d[10] = bs; d[11] = slot;
+          }
+          link = 0;
+        }
         set4(nn, j, link);
       }
       T.tv[base + b] = vv;
       T.tn[base + b] = nn;
     }
+    __syncwarp();
     // phase 3: retire the region; dead slots redirect to the first new simplex
-    for (int h = 0; h < nc; h++) {
+    for (int h = lane; h < nc; h += 32) {
       int t = C[h];
       *comp_ptr(T.tv, t, 0) = DEAD;
       *comp_ptr(T.tn, t, 0) = pack_nb(base, 0);
     }
-    T.state[p] = 1;
-    T.loc[p] = base;
-    atomicAdd(S.count + 2, 1);
+    if (lane == 0) {
+      T.state[p] = 1;
+      T.loc[p] = base;
+      atomicAdd(nwin, 1);
+    }
+    __syncwarp();
   }
 }
 
@@ -361,29 +445,79 @@ __device__ int walk_to(const TriView<D>& T, int s, int p, int limit) {
   return -1;
 }
 
+// Keeps uninserted points for the next round; points whose simplex died go
+// to the walker list, the others make the next round's pick right away.
 template <int D>
-__global__ void k_relocate(TriView<D> T, const int* act, int nact, int* act_out, int* nact_out, unsigned next_round) {
+__global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, int* act_out, int* nact_out,
+                              int* walk, int* nwalk, unsigned next_round) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  bool keep = false;
+  int nact = *nact_p;
+  bool keep = false, walker = false;
   int p = -1;
   if (idx < nact) {
     p = act[idx];
     if (T.state[p] == 0) {
       keep = true;
       int s = T.loc[p];
-      int4 vv = T.tv[s];
-      if (vv.x == DEAD) {
-        s = nb_simplex(T.tn[s].x);
-        int r = walk_to(T, s, p, 1 << 22);
-        if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); r = 0; keep = false; }
-        T.loc[p] = r;
-        s = r;
-      }
-      // the next round's pick
-      if (keep) atomicMax(&T.claimC[s], mkkey(next_round, p));
+      if (*comp_ptr(T.tv, s, 0) == DEAD) walker = true;
+      else atomicMax(&T.claimC[s], mkkey(next_round, p));
     }
   }
   warp_append(act_out, nact_out, keep, p);
+  warp_append(walk, nwalk, walker, p);
+}
+
+// Opt-in self-check of the mesh (GDT_CHECK): every live simplex's links are
+// symmetric and neighbours share the facet's vertices.
+template <int D>
+__global__ void k_check_mesh(TriView<D> T, const int* toff, const int* tcount, int ninst, unsigned round) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= T.nslots) return;
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) { int mid = (lo + hi + 1) >> 1; if (toff[mid] <= s) lo = mid; else hi = mid - 1; }
+  if (s >= tcount[lo]) return;
+  int4 v = T.tv[s];
+  if (v.x == DEAD) return;
+  int4 n = T.tn[s];
+  for (int i = 0; i <= D; i++) {
+    int x = get4(n, i);
+    int u = nb_simplex(x), f = nb_face(x);
+    bool bad = !slot_ok(T, u);
+    if (!bad) {
+      int4 w = T.tv[u];
+      bad = w.x == DEAD || get4(T.tn[u], f) != pack_nb(s, i);
+      if (!bad) {
+        for (int a = 0; a <= D; a++) {
+          if (a == i) continue;
+          bool found = false;
+          for (int b = 0; b <= D; b++) if (b != f && get4(w, b) == get4(v, a)) found = true;
+          bad |= !found;
+        }
+      }
+    }
+    if (bad && atomicCAS(&T.st->error, 0, DT_E_INTERNAL) == 0) {
+      T.st->detail = 30;
+      int* d = T.st->dbg;
+      d[0] = (int)round; d[1] = s; d[2] = i; d[3] = x; d[4] = v.x; d[5] = v.y; d[6] = v.z; d[7] = v.w;
+    }
+  }
+}
+
+template <int D>
+__global__ void k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p, unsigned next_round) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= *nwalk_p) return;
+  int p = walk[idx];
+  int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
+  int r = walk_to(T, s, p, 1 << 22);
+  if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); return; }
+  T.loc[p] = r;
+  atomicMax(&T.claimC[r], mkkey(next_round, p));
+}
+
+__global__ void k_move_count(int* dst, int* src) {
+  *dst = *src;
+  *src = 0;
 }
 
 // ---------------------------------------------------------------- host
@@ -498,21 +632,30 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     int* h = c->counters_host;
     CUDA_OK(cudaMemcpyAsync(h, cnt, 4, cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
-    int nact = h[0];
+    int nact = h[0];            // an upper bound between synchronisations
     // candidate scratch
     int capC = D == 2 ? 32 : 96, capB = D == 2 ? 48 : 192;
     if (c->cfg.cavity_cap > 0) {
       capC = c->cfg.cavity_cap;
       capB = D == 2 ? c->cfg.cavity_cap * 3 / 2 : c->cfg.cavity_cap * 2;
     }
+    int* nom = (int*)pool_get(c, "eng.nom", 4 * std::max<int64_t>(npts, 1));
+    int* walk = (int*)pool_get(c, "eng.walk", 4 * std::max<int64_t>(npts, 1));
+    if (!nom || !walk) return set_err(c, DT_E_NOMEM, "nominee lists");
+    // device counters: [0] active, [1] next active, [2] nominees, [3] winners, [4] walkers
     int overflow_grow = 0;
     bool failed = false;
     int* ain = act0;
     int* aout = act1;
     unsigned round = 0;
+    int last_sync_nact = nact;
+    const bool prof = c->cfg.profile != 0;
+    const int SYNC_EVERY = 4;
+    if (nact > 0)
+      k_pick<D><<<(unsigned)ceil_div(nact, 256), 256, (++c->launches, 0), s>>>(T, ain, nact, 1);
     while (nact > 0) {
       round++;
-      if (round > 200000) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
+      if (round > 400000) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
       int capCand = (int)std::min<int64_t>(nact, int64_t(1) << 22);
       CandScratch S;
       S.cap = capCand;
@@ -523,52 +666,61 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       S.cav = (int*)pool_get(c, "eng.cav", 4 * (size_t)capCand * S.capC);
       S.bnd = (int*)pool_get(c, "eng.bnd", 4 * (size_t)capCand * S.capB);
       S.outer = (int*)pool_get(c, "eng.outer", 4 * (size_t)capCand * S.capB);
-      S.count = cnt + 4;
+      S.count = cnt + 2;
       if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
-      CUDA_OK(cudaMemsetAsync(cnt + 4, 0, 16, s));
-      unsigned nb = (unsigned)ceil_div(nact, 256);
-      const bool prof = c->cfg.profile != 0;
+      CUDA_OK(cudaMemsetAsync(cnt + 1, 0, 16, s));
+      unsigned gp = (unsigned)ceil_div(nact, 256);
+      unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
       if (prof) cudaEventRecord(c->pev[0], s);
-      if (round == 1) k_pick<D><<<nb, 256, (++c->launches, 0), s>>>(T, ain, nact, round);
+      k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2);
       if (prof) cudaEventRecord(c->pev[1], s);
-      k_cavity<D><<<(unsigned)ceil_div(nact, 128), 128, (++c->launches, 0), s>>>(T, ain, nact, round, S);
+      k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S);
       if (prof) cudaEventRecord(c->pev[2], s);
-      unsigned ib = (unsigned)std::min<int64_t>(ceil_div<int64_t>(capCand, 128), 152 * 16);
-      k_insert<D><<<ib, 128, (++c->launches, 0), s>>>(T, round, S);
+      k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3);
       if (prof) cudaEventRecord(c->pev[3], s);
-      k_relocate<D><<<nb, 256, (++c->launches, 0), s>>>(T, ain, nact, aout, cnt + 5, round + 1);
+      k_reloc_check<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, aout, cnt + 1, walk, cnt + 4, round + 1);
+      k_reloc_walk<D><<<gp, 256, (++c->launches, 0), s>>>(T, walk, cnt + 4, round + 1);
       if (prof) cudaEventRecord(c->pev[4], s);
-      CUDA_OK(cudaMemcpyAsync(h, cnt + 5, 4, cudaMemcpyDeviceToHost, s));
-      CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-      CUDA_OK(cudaStreamSynchronize(s));
-      if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { failed = true; break; }
-      if (c->status_host->error) return check_status(c, "insertion round");
+      if (getenv("GDT_DEBUG")) {
+        int hc[5];
+        cudaMemcpyAsync(hc, cnt, 20, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        fprintf(stderr, "round %u nact %d cand %d win %d walk %d\n", round, hc[0], hc[2], hc[3], hc[4]);
+      }
+      k_move_count<<<1, 1, (++c->launches, 0), s>>>(cnt + 0, cnt + 1);
+      std::swap(ain, aout);
+      const bool check = getenv("GDT_CHECK") != nullptr;
+      if (check)
+        k_check_mesh<D><<<(unsigned)ceil_div<int64_t>(total, 256), 256, (++c->launches, 0), s>>>(
+            T, run.toff, run.tcount, ninst, round);
       if (prof) {
-        const char* names[4] = {D == 2 ? "k_pick<2>" : "k_pick<3>", D == 2 ? "k_cavity<2>" : "k_cavity<3>",
-                                D == 2 ? "k_insert<2>" : "k_insert<3>", D == 2 ? "k_relocate<2>" : "k_relocate<3>"};
+        CUDA_OK(cudaStreamSynchronize(s));
+        const char* names[4] = {D == 2 ? "k_nominate<2>" : "k_nominate<3>", D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>",
+                                D == 2 ? "k_insert_w<2>" : "k_insert_w<3>", D == 2 ? "k_reloc<2>" : "k_reloc<3>"};
         for (int q = 0; q < 4; q++) {
           float ms = 0;
           cudaEventElapsedTime(&ms, c->pev[q], c->pev[q + 1]);
           prof_add(c, names[q], ms, 0, 0);
         }
       }
+      if (round % SYNC_EVERY != 0 && nact > 4096 && !check) continue;
+      CUDA_OK(cudaMemcpyAsync(h, cnt + 0, 4, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { failed = true; break; }
+      if (c->status_host->error) return check_status(c, "insertion round");
       int nnew = h[0];
-      if (getenv("GDT_DEBUG")) {
-        int hc[4];
-        cudaMemcpy(hc, cnt + 4, 16, cudaMemcpyDeviceToHost);
-        fprintf(stderr, "round %u nact %d cand %d win %d\n", round, nact, hc[0], hc[2]);
-      }
-      if (nnew == nact) {
-        // no insertion anywhere: only possible when candidates overflowed their scratch
+      if (nnew == last_sync_nact) {
+        // no insertion since the last check: only possible when nominees overflowed their scratch
         if (c->status_host->overflow_cav && overflow_grow < 8) {
           overflow_grow++;
           CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));
         } else {
-          return set_err(c, DT_E_INTERNAL, "insertion round made no progress");
+          return set_err(c, DT_E_INTERNAL, "insertion rounds made no progress");
         }
       }
       nact = nnew;
-      std::swap(ain, aout);
+      last_sync_nact = nnew;
     }
     run.rounds = (int)round;
     if (failed) { grow *= 2; continue; }
@@ -577,7 +729,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       CUDA_OK(cudaMemcpyAsync(hp, profc, 16, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
       // insphere filter: about 145 FP64 operations in 3D, 40 in 2D
-      prof_add(c, D == 2 ? "k_cavity<2>" : "k_cavity<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 40 : 145));
+      prof_add(c, D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 40 : 145));
     }
     run.h_status.assign(ninst, 0);
     run.h_tcount.assign(ninst, 0);

@@ -224,6 +224,93 @@ static int run_dc(dt_ctx* c, const void* P, int64_t n, int dim, int k, double fr
   return 0;
 }
 
+// ---------------------------------------------------------------- batches
+__global__ void k_inst_of_point(const long long* off, int count, int64_t n, int* inst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  inst[i] = lo;
+}
+
+// Canonical rows (global indices) -> instance-local indices, per-instance counts.
+template <int D>
+__global__ void k_rows_to_local(int32_t* rows, int64_t nrows, const long long* off, int count, int* icount) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int32_t* row = rows + r * (D + 1);
+  int v0 = row[0];
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= v0) lo = mid; else hi = mid - 1;
+  }
+  int base = (int)off[lo];
+  for (int j = 0; j <= D; j++) row[j] -= base;
+  atomicAdd(&icount[lo], 1);
+}
+
+// Many independent problems in one engine run: instance i is points
+// [offsets[i], offsets[i+1]); each is triangulated directly.
+int run_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count, int dim) {
+  cudaStream_t s = c->stream;
+  int64_t n = offsets[count];
+  std::vector<int64_t> poff(offsets, offsets + count + 1);
+  std::vector<long long> hoff(offsets, offsets + count + 1);
+  long long* doff = (long long*)pool_get(c, "bt.off", 8 * (size_t)(count + 1));
+  int* pinst = (int*)pool_get(c, "bt.pinst", 4 * std::max<int64_t>(n, 1));
+  int* gid = (int*)pool_get(c, "bt.gid", 4 * std::max<int64_t>(n, 1));
+  int* icount = (int*)pool_get(c, "bt.icount", 4 * (size_t)(count + 1));
+  int* ipos = (int*)pool_get(c, "bt.ipos", 4 * (size_t)(count + 1));
+  if (!doff || !pinst || !gid || !icount || !ipos) return set_err(c, DT_E_NOMEM, "batch buffers");
+  CUDA_OK(cudaMemcpyAsync(doff, hoff.data(), 8 * (size_t)(count + 1), cudaMemcpyHostToDevice, s));
+  unsigned g = (unsigned)ceil_div<int64_t>(std::max<int64_t>(n, 1), 256);
+  k_inst_of_point<<<g, 256, (++c->launches, 0), s>>>(doff, count, n, pinst);
+  void* P = nullptr;
+  int rc = stage_points(c, points, n, dim, &P, "in", pinst);
+  if (rc) return rc;
+  k_iota<<<g, 256, (++c->launches, 0), s>>>(gid, n, 0);
+  cudaEventRecord(c->ev[4], s);
+  rc = engine_run(c, c->run_parts, dim, P, gid, pinst, n, poff, "parts");
+  if (rc) return rc;
+  cudaEventRecord(c->ev[5], s);
+  c->stats.rounds_max = c->run_parts.rounds;
+  int4* rows;
+  int64_t nrows;
+  rc = collect_finite(c, c->run_parts, gid, nullptr, 0, &rows, &nrows, "final");
+  if (rc) return rc;
+  rc = canonicalize_rows(c, dim, rows, nrows, std::max<int64_t>(n, 1), &c->out, &c->nout, "final");
+  if (rc) return rc;
+  CUDA_OK(cudaMemsetAsync(icount, 0, 4 * (size_t)(count + 1), s));
+  if (nrows) {
+    unsigned gr = (unsigned)ceil_div<int64_t>(nrows, 256);
+    if (dim == 2) k_rows_to_local<2><<<gr, 256, (++c->launches, 0), s>>>(c->out, nrows, doff, count, icount);
+    else k_rows_to_local<3><<<gr, 256, (++c->launches, 0), s>>>(c->out, nrows, doff, count, icount);
+  }
+  int total = 0;
+  rc = exclusive_scan_i32(c, icount, ipos, count + 1, &total);
+  if (rc) return rc;
+  std::vector<int> hp(count + 1);
+  CUDA_OK(cudaMemcpyAsync(hp.data(), ipos, 4 * (size_t)(count + 1), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  c->batch_offsets.assign(hp.begin(), hp.end());
+  c->batch_status.assign(count, 0);
+  for (int i = 0; i < count; i++)
+    c->batch_status[i] = c->run_parts.h_status[i] == 0 ? 0 : (c->run_parts.h_status[i] == 1 ? DT_E_DEGENERATE : DT_E_ARG);
+  c->batch_count = count;
+  c->stats.ms_phase[2] = ev_ms(c, 4, 5);
+  c->labels = nullptr;
+  c->sample = nullptr;
+  c->sample_block = nullptr;
+  c->border_vtx = nullptr;
+  c->eta = 0;
+  c->n_border = 0;
+  return check_status(c, "batch");
+}
+
 int run_pipeline(dt_ctx* c, const double* points, int64_t n, int dim, int k, double frac) {
   void* P = nullptr;
   int rc = stage_points(c, points, n, dim, &P, "in");

@@ -56,7 +56,9 @@ int check_status(dt_ctx* c, const char* where) {
   int code = c->status_host->error;
   if (code) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s: device error %d (check %d)", where, code, c->status_host->detail);
+    const int* d = c->status_host->dbg;
+    snprintf(buf, sizeof(buf), "%s: device error %d (check %d) [%d %d %d %d %d %d %d %d %d %d %d %d]", where, code,
+             c->status_host->detail, d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8], d[9], d[10], d[11]);
     return set_err(c, code, buf);
   }
   return 0;

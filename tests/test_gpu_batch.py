@@ -1,0 +1,85 @@
+"""GPU parity of the batched form: many independent instances in one engine
+run, each bit-identical to the oracle's DT of that instance."""
+import numpy as np
+import pytest
+
+import oracle
+import pointsets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tri():
+    from paper_1902_07554_gb300 import Triangulator
+    t = Triangulator(0)
+    yield t
+    t.close()
+
+
+def _mixed(count, seed, lo, hi, dim=2):
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))).astype(np.int64)
+    parts = []
+    for i, m in enumerate(sizes):
+        r = np.random.default_rng(seed * 1000 + i)
+        parts.append(r.random((m, dim)) if r.random() < 0.5 else r.normal(0.5, 0.1, size=(m, dim)))
+    off = np.zeros(count + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    return np.concatenate(parts), off
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batch_matches_oracle_per_instance(tri, dim):
+    P, off = _mixed(60, 3 + dim, 4, 3000, dim)
+    res = tri.triangulate_batch(P, off)
+    st = tri.batch_status(len(off) - 1)
+    for i in range(len(off) - 1):
+        Q = P[off[i]:off[i + 1]]
+        if len(Q) <= dim:
+            assert st[i] != 0 and len(res[i]) == 0
+            continue
+        assert st[i] == 0
+        assert np.array_equal(res[i].astype(np.int64), oracle.delaunay(Q)), i
+
+
+def test_batch_degenerate_and_tiny_instances(tri):
+    a = pointsets.uniform(300, 2, 1)
+    line = np.stack([np.arange(20.0), np.arange(20.0) * 0.5], axis=1)
+    tiny = np.array([[0.0, 0.0], [1.0, 0.0]])
+    grid = pointsets.grid((9, 7), seed=2)
+    P = np.concatenate([a, line, tiny, grid, a])          # the same points again in another instance: allowed
+    off = np.array([0, 300, 320, 322, 385, 685], dtype=np.int64)
+    res = tri.triangulate_batch(P, off)
+    st = tri.batch_status(5)
+    assert list(st) == [0, -3, -1, 0, 0]
+    assert len(res[1]) == 0 and len(res[2]) == 0
+    assert np.array_equal(res[0].astype(np.int64), oracle.delaunay(a))
+    assert np.array_equal(res[4].astype(np.int64), oracle.delaunay(a))
+    assert np.array_equal(res[3].astype(np.int64), oracle.delaunay(grid))
+
+
+def test_batch_rejects_duplicates_inside_an_instance(tri):
+    from paper_1902_07554_gb300 import DTError
+    a = pointsets.uniform(100, 2, 4)
+    a[50] = a[7]
+    with pytest.raises(DTError, match="DUPLICATE"):
+        tri.triangulate_batch(a, np.array([0, 100]))
+
+
+def test_batch2d_4096_full_size_sampled(tri):
+    """The full batched workload (4,096 instances, 256..65,536 points each,
+    uniform or normal by instance seed), checked on a sample of instances."""
+    P, off, kinds = pointsets.batch_instances()
+    res = tri.triangulate_batch(P, off)
+    assert len(res) == 4096
+    rng = np.random.default_rng(0)
+    for i in rng.choice(4096, 12, replace=False):
+        Q = P[off[i]:off[i + 1]]
+        assert np.array_equal(res[i].astype(np.int64), oracle.delaunay(Q)), i
+    # every instance: 2D triangle count identity T = 2 m - 2 - h
+    for i in rng.choice(4096, 200, replace=False):
+        m = off[i + 1] - off[i]
+        T = res[i]
+        h = oracle.hull_vertex_count(T)
+        assert len(T) == 2 * m - 2 - h
