@@ -405,7 +405,6 @@ static __global__ void k_read_pred_counters_capi(unsigned long long* calls, int*
   *calls = g_exact_calls;
   *range = g_range_error;
   g_exact_calls = 0;
-  g_range_error = 0;
 }
 }  // namespace gdt
 
@@ -438,6 +437,9 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
     k_iota<<<g, 256, (++c->launches, 0), c->stream>>>(g32, n, 0);
   }
   unsigned gm = (unsigned)ceil_div<int64_t>(m, 128);
+  unsigned long long* ctr = (unsigned long long*)pool_get(c, "pred.ctr", 64);
+  if (!ctr) return set_err(c, DT_E_NOMEM, "predicate counters");
+  k_read_pred_counters_capi<<<1, 1, (++c->launches, 0), c->stream>>>(ctr + 2, (int*)(ctr + 3));
   if (dim == 2) {
     k_pack_points<2><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double2*)P, flags);
     k_eval_pred<2><<<gm, 128, (++c->launches, 0), c->stream>>>((const double2*)P, g32, kind, tup, m, (int)n, o, flags + 1);
@@ -445,16 +447,15 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
     k_pack_points<3><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double4_32a*)P, flags);
     k_eval_pred<3><<<gm, 128, (++c->launches, 0), c->stream>>>((const double4_32a*)P, g32, kind, tup, m, (int)n, o, flags + 1);
   }
-  unsigned long long* ctr = (unsigned long long*)pool_get(c, "pred.ctr", 32);
-  if (!ctr) return set_err(c, DT_E_NOMEM, "predicate counters");
   k_read_pred_counters_capi<<<1, 1, (++c->launches, 0), c->stream>>>(ctr, (int*)(ctr + 1));
   int h[2];
-  unsigned long long hc[2];
+  unsigned long long hc[4];
   CUDA_OK(cudaMemcpyAsync(h, flags, 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_OK(cudaMemcpyAsync(hc, ctr, 16, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(cudaMemcpyAsync(hc, ctr, 32, cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(cudaStreamSynchronize(c->stream));
   c->stats.exact_calls = (int32_t)std::min<unsigned long long>(hc[0], 0x7fffffffull);
   if (h[1]) return set_err(c, DT_E_ARG, "tuple index out of range");
-  if ((int)(hc[1] & 0xffffffff)) return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
+  if ((int)(hc[1] & 0xffffffff) != (int)(hc[3] & 0xffffffff))
+    return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
   return copy_out(c, out, o, m);
 }

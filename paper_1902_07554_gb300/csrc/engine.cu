@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "sort.cuh"
 
 namespace gdt {
 
@@ -137,14 +138,32 @@ __global__ void k_init(TriView<D> T, int ninst, const long long* poff, const int
 
 // Initial conflict simplex of every other point: a ghost whose hull facet it
 // lies strictly beyond, else the initial simplex (it lies in it, closed).
+// Activation level of a point: the number of leading zeros of a hash of its
+// global index (P(level >= L) = 2^-L).  Points are activated in batches of
+// decreasing level, so the set of points taking part doubles batch by batch
+// (a randomized insertion order with a growing prefix, as in biased randomized
+// insertion orders).  -1: not to be inserted (initial simplex / bad instance).
+template <int D>
+__global__ void k_levels(TriView<D> T, int64_t npts, const int* inst_status, int* level) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  int l = -1;
+  if (inst_status[T.pinst[p]] == 0 && T.state[p] == 0)
+    l = __clz((int)fmix32((uint32_t)T.gid[p] * 0x9E3779B1u + 0x7F4A7C15u));
+  level[p] = l;
+}
+
 template <int D>
 __global__ void k_locate_init(TriView<D> T, int64_t npts, const int* toff, const int* inst_status,
-                              int* act, int* nact) {
+                              const int* level, int min_level, int* act, int* nact) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool active = false;
   if (p < npts) {
     int i = T.pinst[p];
     if (inst_status[i] == 0 && T.state[p] == 0) {
+      T.loc[p] = toff[i];                  // dormant points wait on the initial simplex
+    }
+    if (inst_status[i] == 0 && T.state[p] == 0 && level[p] >= min_level) {
       active = true;
       int s0 = toff[i];
       int4 vv = T.tv[s0];
@@ -408,7 +427,7 @@ __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, 
 // Visibility walk to a simplex in conflict with point p: a finite simplex
 // containing p (closed), or a ghost entered through its hull facet.
 template <int D>
-__device__ int walk_to(const TriView<D>& T, int s, int p, int limit) {
+__device__ int walk_to(const TriView<D>& T, int s, int p, int limit, int* steps_out = nullptr) {
   if (!slot_ok(T, s)) return -1;
   int4 vv = T.tv[s];
   for (int i = 0; i <= D; i++)
@@ -436,6 +455,7 @@ __device__ int walk_to(const TriView<D>& T, int s, int p, int limit) {
         break;
       }
     }
+    if (steps_out) (*steps_out)++;
     if (next < 0) return s;
     if (!slot_ok(T, next)) return -1;
     s = next;
@@ -465,6 +485,38 @@ __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, i
   }
   warp_append(act_out, nact_out, keep, p);
   warp_append(walk, nwalk, walker, p);
+  if (T.prof && idx < nact) {
+    // act 4, state 1, loc 4, slot word 4, pick 8, output 4
+    unsigned long long b = 25;
+    for (int off = 16; off; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[2], b);
+  }
+}
+
+// Activates a batch of dormant points: from the simplex each was parked on,
+// follow the redirects of dead simplices to a live one, walk to a simplex in
+// conflict with the point, make its pick for the next round, and append it
+// to the active list.
+template <int D>
+__global__ void k_activate(TriView<D> T, const int* list, int m, int* act, int* nact, unsigned next_round) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = false;
+  int p = -1;
+  if (idx < m) {
+    p = list[idx];
+    int s = T.loc[p];
+    for (int hop = 0; hop < (1 << 20) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
+      s = nb_simplex(*comp_ptr(T.tn, s, 0));
+    int r = walk_to(T, s, p, 1 << 22);
+    if (r < 0) {
+      set_error(T.st, DT_E_TIMEOUT, 4);
+    } else {
+      T.loc[p] = r;
+      atomicMax(&T.claimC[r], mkkey(next_round, p));
+      ok = true;
+    }
+  }
+  warp_append(act, nact, ok, p);
 }
 
 // Opt-in self-check of the mesh (GDT_CHECK): every live simplex's links are
@@ -509,10 +561,18 @@ __global__ void k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p, 
   if (idx >= *nwalk_p) return;
   int p = walk[idx];
   int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
-  int r = walk_to(T, s, p, 1 << 22);
+  int steps = 0;
+  int r = walk_to(T, s, p, 1 << 22, &steps);
   if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); return; }
   T.loc[p] = r;
   atomicMax(&T.claimC[r], mkkey(next_round, p));
+  // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
+  if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
+}
+
+__global__ void k_scatter_levels(const int* level, const int* rank, const int* loff, int64_t n, int* list) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < n && level[p] >= 0) list[loff[level[p]] + rank[p]] = (int)p;
 }
 
 __global__ void k_move_count(int* dst, int* src) {
@@ -524,7 +584,7 @@ __global__ void k_move_count(int* dst, int* src) {
 static __global__ void k_read_pred_counters(unsigned long long* calls, int* range, int reset) {
   *calls = g_exact_calls;
   *range = g_range_error;
-  if (reset) { g_exact_calls = 0; g_range_error = 0; }
+  if (reset) g_exact_calls = 0;
 }
 
 void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops) {
@@ -571,6 +631,8 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     int64_t total = run.h_toff[ninst];
     if (total >= (int64_t(1) << 29)) return set_err(c, DT_E_NOMEM, "simplex arena exceeds 2^29 slots");
     run.total_slots = total;
+    unsigned long long calls0; int range0;
+    { int rc0 = pred_counters_engine(c, &calls0, &range0, false); if (rc0) return rc0; }
     run.tv = pool_get(c, tag + ".tv", sizeof(int4) * total);
     run.tn = pool_get(c, tag + ".tn", sizeof(int4) * total);
     auto* claimA = (unsigned long long*)pool_get(c, tag + ".cA", 8 * total);
@@ -626,13 +688,42 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     }
 
     k_init<D><<<ceil_div(ninst, 64), 64, (++c->launches, 0), s>>>(T, ninst, dpoff, run.toff, run.inst_status);
-    if (npts > 0)
-      k_locate_init<D><<<(unsigned)ceil_div<int64_t>(npts, 256), 256, (++c->launches, 0), s>>>(T, npts, run.toff,
-                                                                             run.inst_status, act0, cnt);
+    // activation levels and the per-level lists of dormant points
+    int* level = (int*)pool_get(c, tag + ".level", 4 * std::max<int64_t>(npts, 1));
+    int* lrank = (int*)pool_get(c, "eng.lrank", 4 * std::max<int64_t>(npts, 1));
+    int* lsize = (int*)pool_get(c, "eng.lsize", 4 * 64);
+    int* llist = (int*)pool_get(c, tag + ".llist", 4 * std::max<int64_t>(npts, 1));
+    int* loffd = (int*)pool_get(c, "eng.loff", 4 * 64);
+    if (!level || !lrank || !lsize || !llist || !loffd) return set_err(c, DT_E_NOMEM, "activation levels");
+    std::vector<int64_t> loff(34, 0);
+    int first_level = 0;
+    if (npts > 0) {
+      unsigned gpp = (unsigned)ceil_div<int64_t>(npts, 256);
+      k_levels<D><<<gpp, 256, (++c->launches, 0), s>>>(T, npts, run.inst_status, level);
+      int rc = group_rank(c, level, npts, lrank, lsize, 33);
+      if (rc) return rc;
+      int hs[33];
+      CUDA_OK(cudaMemcpyAsync(hs, lsize, 4 * 33, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      for (int l = 0; l < 33; l++) loff[l + 1] = loff[l] + hs[l];
+      std::vector<int> lo32(34);
+      for (int l = 0; l < 34; l++) lo32[l] = (int)loff[l];
+      CUDA_OK(cudaMemcpyAsync(loffd, lo32.data(), 4 * 34, cudaMemcpyHostToDevice, s));
+      k_scatter_levels<<<gpp, 256, (++c->launches, 0), s>>>(level, lrank, loffd, npts, llist);
+      // the first batch: about 64 points per instance (at least 4096 in all)
+      int64_t want = std::max<int64_t>(4096, 64 * (int64_t)ninst);
+      first_level = 32;
+      while (first_level > 0 && loff[33] - loff[first_level] < want) first_level--;
+      if (getenv("GDT_NOBRIO")) first_level = 0;
+      k_locate_init<D><<<gpp, 256, (++c->launches, 0), s>>>(T, npts, run.toff, run.inst_status, level, first_level,
+                                                            act0, cnt);
+    }
+    int next_level = first_level - 1;    // next batch to activate (levels below are later)
     int* h = c->counters_host;
     CUDA_OK(cudaMemcpyAsync(h, cnt, 4, cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
     int nact = h[0];            // an upper bound between synchronisations
+    int last_batch = nact;
     // candidate scratch
     int capC = D == 2 ? 32 : 96, capB = D == 2 ? 48 : 192;
     if (c->cfg.cavity_cap > 0) {
@@ -653,7 +744,20 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     const int SYNC_EVERY = 4;
     if (nact > 0)
       k_pick<D><<<(unsigned)ceil_div(nact, 256), 256, (++c->launches, 0), s>>>(T, ain, nact, 1);
-    while (nact > 0) {
+    while (nact > 0 || next_level >= 0) {
+      // activate the next batch when the active set has drained to a quarter
+      while (next_level >= 0 && nact <= last_batch / 4) {
+        int m = (int)(loff[next_level + 1] - loff[next_level]);
+        if (m > 0) {
+          k_activate<D><<<(unsigned)ceil_div(m, 256), 256, (++c->launches, 0), s>>>(
+              T, llist + loff[next_level], m, ain, cnt + 0, round + 1);
+          nact += m;
+          last_batch = nact;
+          last_sync_nact = -1;         // activation changes the count: skip one progress check
+        }
+        next_level--;
+      }
+      if (nact <= 0) break;
       round++;
       if (round > 400000) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
       int capCand = (int)std::min<int64_t>(nact, int64_t(1) << 22);
@@ -710,7 +814,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { failed = true; break; }
       if (c->status_host->error) return check_status(c, "insertion round");
       int nnew = h[0];
-      if (nnew == last_sync_nact) {
+      if (nnew == last_sync_nact && nnew > 0) {
         // no insertion since the last check: only possible when nominees overflowed their scratch
         if (c->status_host->overflow_cav && overflow_grow < 8) {
           overflow_grow++;
@@ -722,6 +826,11 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       nact = nnew;
       last_sync_nact = nnew;
     }
+    if (c->status_host->error == 0) {
+      CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      if (c->status_host->error) return check_status(c, "activation");
+    }
     run.rounds = (int)round;
     if (failed) { grow *= 2; continue; }
     if (profc) {
@@ -730,6 +839,10 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       CUDA_OK(cudaStreamSynchronize(s));
       // insphere filter: about 145 FP64 operations in 3D, 40 in 2D
       prof_add(c, D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 40 : 145));
+      unsigned long long hr = 0;
+      CUDA_OK(cudaMemcpyAsync(&hr, profc + 2, 8, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      prof_add(c, D == 2 ? "k_reloc<2>" : "k_reloc<3>", 0, (double)hr, 0);
     }
     run.h_status.assign(ninst, 0);
     run.h_tcount.assign(ninst, 0);
@@ -739,7 +852,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     unsigned long long calls; int range;
     int rc = pred_counters_engine(c, &calls, &range, false);
     if (rc) return rc;
-    if (range) return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
+    if (range != range0) return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
     return 0;
   }
   return set_err(c, DT_E_OVERFLOW, "simplex arena overflow after retries");

@@ -19,7 +19,11 @@
 namespace gdt {
 
 // Per translation unit (no relocatable device code): each unit that uses the
-// predicates exposes its own reader/resetter of these two words.
+// predicates exposes its own reader of these two words.  g_range_error counts
+// exact evaluations that exceeded the widest integer format; it is never
+// reset, so a caller compares its value before and after its own work (with
+// several contexts at once an increase may come from another one: the error
+// is then reported conservatively).
 static __device__ unsigned long long g_exact_calls;
 static __device__ int g_range_error;
 
@@ -353,7 +357,7 @@ static __device__ __noinline__ int exact_dispatch(int kind, int D, const double*
       default: return ex_coplanar<16>(kind - 3, dv, emin);
     }
   }
-  atomicExch(&g_range_error, 1);
+  atomicAdd(&g_range_error, 1);
   return 1;
 }
 
@@ -636,7 +640,7 @@ static __device__ __noinline__ int closer_exact(P p, P a, P b, int D) {
   int nl = limbs_for(s, 2);
   if (nl <= 4) return ex_closer<4>(D, dv, s.emin);
   if (nl <= 16) return ex_closer<16>(D, dv, s.emin);
-  atomicExch(&g_range_error, 1);
+  atomicAdd(&g_range_error, 1);
   return 0;
 }
 template <typename P>
