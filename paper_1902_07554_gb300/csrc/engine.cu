@@ -64,6 +64,31 @@ __device__ __forceinline__ bool verts_ok(const TriView<D>& T, const int4& v) {
 }
 
 template <int D>
+__device__ __forceinline__ int hint_cell(const TriView<D>& T, int p) {
+  int i = T.pinst[p];
+  const double* g = T.glo + 6 * i;
+  const int* d = T.gdim + 4 * i;
+  typename PT<D>::T q = T.pts[p];
+  int id = 0;
+  for (int c = D - 1; c >= 0; c--) {
+    double f = (comp(q, c) - g[c]) * g[3 + c];
+    int x = f < 0 ? 0 : (f >= d[c] ? d[c] - 1 : (int)f);
+    id = id * d[c] + x;
+  }
+  return d[3] + id;
+}
+
+template <int D>
+__device__ __forceinline__ int inst_of_slot_e(const TriView<D>& T, int s) {
+  int lo = 0, hi = T.ninst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (T.toff[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D>
 __device__ __forceinline__ int orient_tuple(const TriView<D>& T, const int4& v) {
   int t[4] = {v.x, v.y, v.z, v.w};
   return orient_p(T.pts, t);
@@ -223,7 +248,7 @@ __global__ void k_nominate(TriView<D> T, const int* act, const int* nact_p, unsi
 // returned old value also deduplicates lanes that reach the same simplex),
 // the others become boundary facets (ring claim in claimA).
 template <int D>
-__global__ void __launch_bounds__(128) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
+__global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
                                                   CandScratch S) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
@@ -419,6 +444,7 @@ __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, 
       T.state[p] = 1;
       T.loc[p] = base;
       atomicAdd(nwin, 1);
+      if (T.hint) T.hint[hint_cell(T, p)] = base;
     }
     __syncwarp();
   }
@@ -489,7 +515,7 @@ __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, i
     // act 4, state 1, loc 4, slot word 4, pick 8, output 4
     unsigned long long b = 25;
     for (int off = 16; off; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[2], b);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[3], b);
   }
 }
 
@@ -498,13 +524,17 @@ __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, i
 // conflict with the point, make its pick for the next round, and append it
 // to the active list.
 template <int D>
-__global__ void k_activate(TriView<D> T, const int* list, int m, int* act, int* nact, unsigned next_round) {
+__global__ void __launch_bounds__(128, 8) k_activate(TriView<D> T, const int* list, int m, int* act, int* nact, unsigned next_round) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = false;
   int p = -1;
   if (idx < m) {
     p = list[idx];
     int s = T.loc[p];
+    if (T.hint) {
+      int h = T.hint[hint_cell(T, p)];
+      if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
+    }
     for (int hop = 0; hop < (1 << 20) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
       s = nb_simplex(*comp_ptr(T.tn, s, 0));
     int r = walk_to(T, s, p, 1 << 22);
@@ -556,7 +586,7 @@ __global__ void k_check_mesh(TriView<D> T, const int* toff, const int* tcount, i
 }
 
 template <int D>
-__global__ void k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p, unsigned next_round) {
+__global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p, unsigned next_round) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= *nwalk_p) return;
   int p = walk[idx];
@@ -568,6 +598,26 @@ __global__ void k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p, 
   atomicMax(&T.claimC[r], mkkey(next_round, p));
   // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
   if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
+}
+
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x + 0.0);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__global__ void k_ubox_init(unsigned long long* ub, int ninst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 6 * ninst) ub[i] = (i % 6) < 3 ? ~0ull : 0ull;
+}
+template <int D>
+__global__ void k_inst_bbox(TriView<D> T, int64_t npts, unsigned long long* ub) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  int i = T.pinst[p];
+  for (int c = 0; c < D; c++) {
+    unsigned long long k = ord_key(comp(T.pts[p], c));
+    atomicMin(&ub[6 * i + c], k);
+    atomicMax(&ub[6 * i + 3 + c], k);
+  }
 }
 
 __global__ void k_scatter_levels(const int* level, const int* rank, const int* loff, int64_t n, int* list) {
@@ -585,6 +635,13 @@ static __global__ void k_read_pred_counters(unsigned long long* calls, int* rang
   *calls = g_exact_calls;
   *range = g_range_error;
   if (reset) g_exact_calls = 0;
+}
+
+static double host_from_orderable(unsigned long long u) {
+  unsigned long long b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
 }
 
 void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops) {
@@ -688,6 +745,57 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     }
 
     k_init<D><<<ceil_div(ninst, 64), 64, (++c->launches, 0), s>>>(T, ninst, dpoff, run.toff, run.inst_status);
+    T.toff = run.toff;
+    T.ninst = ninst;
+    T.hint = nullptr;
+    if (npts > 0 && !getenv("GDT_NOHINT")) {
+      // per-instance bounding boxes -> grids of about n_i / 4 cells
+      unsigned long long* ub = (unsigned long long*)pool_get(c, "eng.ubox", 8 * 6 * (size_t)ninst);
+      double* glo = (double*)pool_get(c, tag + ".glo", 8 * 6 * (size_t)ninst);
+      int* gdim = (int*)pool_get(c, tag + ".gdim", 4 * 4 * (size_t)ninst);
+      if (!ub || !glo || !gdim) return set_err(c, DT_E_NOMEM, "hint grids");
+      k_ubox_init<<<ceil_div(6 * ninst, 128), 128, (++c->launches, 0), s>>>(ub, ninst);
+      k_inst_bbox<D><<<(unsigned)ceil_div<int64_t>(npts, 256), 256, (++c->launches, 0), s>>>(T, npts, ub);
+      std::vector<unsigned long long> hu(6 * (size_t)ninst);
+      CUDA_OK(cudaMemcpyAsync(hu.data(), ub, 8 * 6 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      std::vector<double> hg(6 * (size_t)ninst, 0.0);
+      std::vector<int> hd(4 * (size_t)ninst, 1);
+      int64_t cells = 0;
+      for (int i = 0; i < ninst; i++) {
+        int64_t ni = poff[i + 1] - poff[i];
+        double lo[3], ext[3], vol = 1.0;
+        int nd = 0;
+        for (int cc = 0; cc < D; cc++) {
+          lo[cc] = host_from_orderable(hu[6 * i + cc]);
+          double hi = host_from_orderable(hu[6 * i + 3 + cc]);
+          ext[cc] = (ni > 0 && hi > lo[cc]) ? hi - lo[cc] : 0.0;
+          if (ext[cc] > 0) { vol *= ext[cc]; nd++; }
+        }
+        double target = std::max<double>(1.0, (double)ni / 4.0);
+        double side = nd ? std::pow(vol / target, 1.0 / nd) : 1.0;
+        int64_t ci = 1;
+        for (int cc = 0; cc < 3; cc++) {
+          int d = 1;
+          if (cc < D && ext[cc] > 0 && side > 0) d = (int)std::min(1024.0, std::max(1.0, std::ceil(ext[cc] / side)));
+          hd[4 * i + cc] = d;
+          hg[6 * i + cc] = cc < D && ni > 0 ? lo[cc] : 0.0;
+          hg[6 * i + 3 + cc] = (cc < D && ext[cc] > 0) ? d / ext[cc] : 0.0;
+          ci *= d;
+        }
+        hd[4 * i + 3] = (int)cells;
+        cells += ci;
+      }
+      int* hint = (int*)pool_get(c, tag + ".hint", 4 * std::max<int64_t>(cells, 1));
+      if (!hint) return set_err(c, DT_E_NOMEM, "hint cells");
+      CUDA_OK(cudaMemsetAsync(hint, 0xff, 4 * std::max<int64_t>(cells, 1), s));
+      CUDA_OK(cudaMemcpyAsync(glo, hg.data(), 8 * 6 * (size_t)ninst, cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaMemcpyAsync(gdim, hd.data(), 4 * 4 * (size_t)ninst, cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaStreamSynchronize(s));   // host vectors go out of scope
+      T.hint = hint;
+      T.glo = glo;
+      T.gdim = gdim;
+    }
     // activation levels and the per-level lists of dormant points
     int* level = (int*)pool_get(c, tag + ".level", 4 * std::max<int64_t>(npts, 1));
     int* lrank = (int*)pool_get(c, "eng.lrank", 4 * std::max<int64_t>(npts, 1));
@@ -749,8 +857,16 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       while (next_level >= 0 && nact <= last_batch / 4) {
         int m = (int)(loff[next_level + 1] - loff[next_level]);
         if (m > 0) {
-          k_activate<D><<<(unsigned)ceil_div(m, 256), 256, (++c->launches, 0), s>>>(
+          if (prof) cudaEventRecord(c->pev[6], s);
+          k_activate<D><<<(unsigned)ceil_div(m, 128), 128, (++c->launches, 0), s>>>(
               T, llist + loff[next_level], m, ain, cnt + 0, round + 1);
+          if (prof) {
+            cudaEventRecord(c->pev[7], s);
+            cudaEventSynchronize(c->pev[7]);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->pev[6], c->pev[7]);
+            prof_add(c, D == 2 ? "k_activate<2>" : "k_activate<3>", ms, 0, 0);
+          }
           nact += m;
           last_batch = nact;
           last_sync_nact = -1;         // activation changes the count: skip one progress check
@@ -783,8 +899,9 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3);
       if (prof) cudaEventRecord(c->pev[3], s);
       k_reloc_check<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, aout, cnt + 1, walk, cnt + 4, round + 1);
-      k_reloc_walk<D><<<gp, 256, (++c->launches, 0), s>>>(T, walk, cnt + 4, round + 1);
       if (prof) cudaEventRecord(c->pev[4], s);
+      k_reloc_walk<D><<<(unsigned)ceil_div(nact, 128), 128, (++c->launches, 0), s>>>(T, walk, cnt + 4, round + 1);
+      if (prof) cudaEventRecord(c->pev[5], s);
       if (getenv("GDT_DEBUG")) {
         int hc[5];
         cudaMemcpyAsync(hc, cnt, 20, cudaMemcpyDeviceToHost, s);
@@ -799,9 +916,10 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
             T, run.toff, run.tcount, ninst, round);
       if (prof) {
         CUDA_OK(cudaStreamSynchronize(s));
-        const char* names[4] = {D == 2 ? "k_nominate<2>" : "k_nominate<3>", D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>",
-                                D == 2 ? "k_insert_w<2>" : "k_insert_w<3>", D == 2 ? "k_reloc<2>" : "k_reloc<3>"};
-        for (int q = 0; q < 4; q++) {
+        const char* names[5] = {D == 2 ? "k_nominate<2>" : "k_nominate<3>", D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>",
+                                D == 2 ? "k_insert_w<2>" : "k_insert_w<3>", D == 2 ? "k_reloc_check<2>" : "k_reloc_check<3>",
+                                D == 2 ? "k_reloc_walk<2>" : "k_reloc_walk<3>"};
+        for (int q = 0; q < 5; q++) {
           float ms = 0;
           cudaEventElapsedTime(&ms, c->pev[q], c->pev[q + 1]);
           prof_add(c, names[q], ms, 0, 0);
@@ -839,10 +957,11 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       CUDA_OK(cudaStreamSynchronize(s));
       // insphere filter: about 145 FP64 operations in 3D, 40 in 2D
       prof_add(c, D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 40 : 145));
-      unsigned long long hr = 0;
-      CUDA_OK(cudaMemcpyAsync(&hr, profc + 2, 8, cudaMemcpyDeviceToHost, s));
+      unsigned long long hr[2] = {0, 0};
+      CUDA_OK(cudaMemcpyAsync(hr, profc + 2, 16, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
-      prof_add(c, D == 2 ? "k_reloc<2>" : "k_reloc<3>", 0, (double)hr, 0);
+      prof_add(c, D == 2 ? "k_reloc_walk<2>" : "k_reloc_walk<3>", 0, (double)hr[0], 0);
+      prof_add(c, D == 2 ? "k_reloc_check<2>" : "k_reloc_check<3>", 0, (double)hr[1], 0);
     }
     run.h_status.assign(ninst, 0);
     run.h_tcount.assign(ninst, 0);

@@ -48,6 +48,13 @@ struct TriView {
   int npts;                 // total points (bounds for every vertex)
   unsigned long long* prof; // profile counters (null unless profiling):
                             // [0] bytes touched by k_cavity, [1] its conflict tests
+  // per-instance hint grids: a recently created simplex per cell, used as the
+  // start of the walk when a dormant point is activated
+  int* hint;                // cells of all instances, -1 = none
+  const double* glo;        // per instance: grid origin (3) and inverse cell edge (3)
+  const int* gdim;          // per instance: cells per axis (3) and first cell (1)
+  const int* toff;          // per instance: first simplex slot
+  int ninst;
 };
 
 struct CandScratch {
