@@ -44,6 +44,10 @@ WORKLOADS = {
     "uniform2d_10k": dict(n=10_000, dim=2, gen="uniform", seed=1, k=4, frac=0.01),
     # a smaller case of the same shape, for profiler captures (a few GB on the device)
     "uniform3d_200k": dict(n=200_000, dim=3, gen="uniform", seed=2, k=16, frac=0.005),
+    # 4,096 independent 2D instances, 256..65,536 points each (log-uniform)
+    "batch2d_4096": dict(n=0, dim=2, gen="batch", seed=4, k=1, frac=0.0),
+    # Poisson arrivals of 3D jobs, 1,000..2,000,000 points, uniform or clustered
+    "serve3d": dict(n=0, dim=3, gen="serve", seed=5, k=0, frac=0.005, jobs=120, load=0.8),
 }
 
 
@@ -63,6 +67,11 @@ def job_value(n_per_rank: int, world: int, ms_max: float) -> float:
 
 
 def gen_points(w, seed_offset=0):
+    if w["gen"] == "batch":
+        return pointsets.batch_instances(seed=w["seed"])[0]
+    if w["gen"] == "serve":
+        sizes, kinds, seeds = pointsets.serve_jobs(8, seed=w["seed"])
+        return pointsets.job_points(min(int(sizes[0]), 200_000), kinds[0], seeds[0])
     if w["gen"] == "uniform":
         return pointsets.uniform(w["n"], w["dim"], w["seed"] + seed_offset)
     return pointsets.clustered(w["n"], w["seed"] + seed_offset)
@@ -151,7 +160,9 @@ def run_reference(args, w):
         return 0
     import oracle
     P = gen_points(w)
-    m = min(w["n"], 60_000 if w["dim"] == 3 else 300_000)
+    if w["gen"] == "batch":
+        P = P[:65_536]                     # the first instances of the batch (2D)
+    m = min(len(P), 60_000 if w["dim"] == 3 else 300_000)
     sample = P[:m]
     for _ in range(args.warmup):
         oracle.delaunay(sample[: m // 10])
@@ -168,8 +179,116 @@ def run_reference(args, w):
             "config": {"workload": args.workload, "n": w["n"], "dim": w["dim"], "k": w["k"],
                        "sample_frac": w["frac"], "reference_sample_points": m},
             "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {m} of the {w['n']} workload points per step"},
+                             "sample": f"first {m} points of the workload per step, one full DT by the C oracle"},
             "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args, w):
+    """Batched form: all instances in one dt_triangulate_batch per step."""
+    import torch
+    from paper_1902_07554_gb300 import Triangulator
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    P, off, kinds = pointsets.batch_instances(seed=w["seed"])
+    n = int(off[-1])
+    tri = Triangulator(local, stream=stream.cuda_stream)
+    P_dev = torch.from_numpy(P).to(f"cuda:{local}")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        tri.L.dt_triangulate_batch(tri.ctx, ctypes_ptr(P_dev), ctypes_ptr(off), len(off) - 1, 2)
+    clk = ClockSampler(local)
+    clk.start()
+    step_ms, launches = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = tri.L.dt_triangulate_batch(tri.ctx, ctypes_ptr(P_dev), ctypes_ptr(off), len(off) - 1, 2)
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, tri.L.dt_last_error(tri.ctx)
+        step_ms.append(e0.elapsed_time(e1))
+        launches += tri.stats().launches
+    clocks = clk.stop()
+    ms = sum(step_ms) / len(step_ms)
+    # end to end from pinned host memory, results back on the host
+    P_pin = torch.from_numpy(P).pin_memory()
+    e2e = []
+    for _ in range(max(2, args.steps // 2)):
+        t = time.perf_counter()
+        res = tri.triangulate_batch(P_pin, off)
+        e2e.append(time.perf_counter() - t)
+    nout = sum(len(r) for r in res)
+    st = tri.stats()
+    line = {"metric": METRIC, "value": n / (ms / 1e3) / 1e6, "unit": "Mpoints/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances": len(off) - 1, "points": n, "dim": 2,
+                       "l2": "flushed before every step (256 MiB write)"},
+            "e2e": {"value": n / (sum(e2e) / len(e2e)) / 1e6, "unit": "Mpoints/s",
+                    "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": nout * 12},
+            "gpu_launches": launches, "clocks": clocks,
+            "stats": {"simplices": nout, "rounds_max": st.rounds_max}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ctypes_ptr(t):
+    import ctypes
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def run_serving(args, w):
+    """Continuous batching vs the plain path (one job at a time, k = 1, no
+    batching) on the same Poisson job stream at `load` x plain capacity."""
+    import torch
+    from paper_1902_07554_gb300 import Triangulator
+    from paper_1902_07554_gb300.serve import Job, Server, k_for, poisson_arrivals
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    sizes, kinds, seeds = pointsets.serve_jobs(w["jobs"], seed=w["seed"])
+    pts = [pointsets.job_points(sizes[i], kinds[i], seeds[i]) for i in range(w["jobs"])]
+    total = int(sum(len(p) for p in pts))
+    # plain path: capacity and service times
+    plain = Triangulator(local)
+    plain.triangulate(pts[0][:5000], k=1, fetch=False)
+    service = []
+    for P in pts:
+        t = time.perf_counter()
+        plain.triangulate(P, k=1, fetch=True)
+        service.append(time.perf_counter() - t)
+    plain.close()
+    cap = total / sum(service)                                  # points per second
+    rate = w["load"] * cap / (total / len(pts))                 # jobs per second
+    arr = poisson_arrivals(len(pts), rate, w["seed"])
+    # plain path under the same arrivals: one server, FIFO
+    free, lat = 0.0, []
+    for a, sv in zip(arr, service):
+        start = max(a, free)
+        free = start + sv
+        lat.append(free - a)
+    lat = np.array(lat)
+    plain_sum = {"throughput_mpts": total / (free - arr[0]) / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "capacity_mpts": cap / 1e6}
+    jobs = [Job(float(arr[i]), i, pts[i], k=k_for(len(pts[i])), frac=w["frac"]) for i in range(len(pts))]
+    srv = Server(device=local, workers=3, budget_bytes=120e9, bytes_per_point=6000.0, keep_results=False)
+    served = srv.run(jobs)
+    line = {"metric": METRIC, "value": served["throughput_mpts"], "unit": "Mpoints/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": served["makespan_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "jobs": len(pts), "points": total, "offered_load": w["load"],
+                       "budget_gb": 120, "workers": 3},
+            "serve": {"served": served, "plain": plain_sum},
+            "e2e": {"value": served["throughput_mpts"], "unit": "Mpoints/s",
+                    "h2d_bytes_per_step": total * 24, "d2h_bytes_per_step": None}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -187,6 +306,10 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if w["gen"] == "batch":
+        return run_batch(args, w)
+    if w["gen"] == "serve":
+        return run_serving(args, w)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
