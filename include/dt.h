@@ -82,10 +82,13 @@ typedef struct dt_config {
   double grid_cell;      /* c_G: grid cell edge in units of the mean point spacing; default 1 */
   uint64_t seed;         /* sample seed; default 1 */
   int base_threshold;    /* N of Alg. 1: run k = 1 when n / k < N; default 2048 */
-  int validate;          /* 1: check every interior facet is locally Delaunay after the merge */
+  int validate;          /* 1: certify the result after the merge (the checks of dt_validate);
+                            a failed certificate returns DT_E_INTERNAL */
   int cavity_cap;        /* initial per-insertion cavity capacity (simplices); 0 = automatic */
   int profile;           /* 1: time the insertion kernels with CUDA events (dt_get_kernel_profile) */
-  int reserved[7];
+  int neighbors;         /* 1: run the neighbourhood update inside dt_triangulate (otherwise it runs
+                            on the first dt_get_neighbors call) */
+  int reserved[6];
 } dt_config;
 
 typedef struct dt_stats {
@@ -105,11 +108,39 @@ typedef struct dt_stats {
   int32_t exact_calls;   /* exact-arithmetic fallbacks taken (saturating) */
   double ms_total;       /* device time of the whole call, ms */
   double ms_phase[8];    /* sample+graph, partition+label+scatter, partial DTs, border,
-                            border DT, merge, canonicalise, validate */
+                            border DT, merge, canonicalise, neighbourhood update + validation */
   int64_t partition_size_max;
   int64_t partition_size_min;
   int64_t launches;      /* CUDA kernels this call launched */
+  int64_t hull_facets;   /* facets of the convex hull (when neighbours were computed) */
+  int32_t validated;     /* 1 when the certificate ran and passed */
+  int32_t reserved_i;
 } dt_stats;
+
+/* Result of a certificate run (dt_validate, dt_config.validate).  The
+ * rows are DT(P) under the perturbation rule exactly when violations == 0:
+ * every simplex is non-flat, every facet lies in one or two simplices, the
+ * two simplices on an interior facet lie on opposite sides of it and each
+ * one's apex is outside the other's perturbed circumsphere (Sec. 2.1, the
+ * Delaunay lemma), the boundary is locally convex at every hull ridge,
+ * every point is a vertex, and the Euler characteristic is 1. */
+typedef struct dt_validation {
+  int64_t simplices;       /* rows checked */
+  int64_t interior_facets; /* facets shared by two rows */
+  int64_t hull_facets;     /* facets of one row only */
+  int64_t edges;           /* distinct edges */
+  int64_t euler;           /* V - E + T (2D) or V - E + F - T (3D) */
+  int64_t bad_index;       /* rows with an index outside [0, n) or a repeated index */
+  int64_t flat;            /* rows of zero orientation */
+  int64_t non_manifold;    /* facets found in more than two rows */
+  int64_t asymmetric;      /* neighbour links that do not match each other */
+  int64_t folded;          /* interior facets whose two rows lie on the same side */
+  int64_t non_delaunay;    /* interior facets that are not locally Delaunay */
+  int64_t non_convex;      /* hull ridges where the boundary bends inwards */
+  int64_t unused_points;   /* input points that are a vertex of no row */
+  int64_t pivot_limit;     /* hull-ridge walks that hit their step limit (4096) */
+  int64_t violations;      /* sum of the eight counters above plus (euler != 1) */
+} dt_validation;
 
 /* One entry of the per-kernel profile (profile mode). */
 typedef struct dt_kernel_profile {
@@ -153,6 +184,28 @@ DT_API int dt_get_simplices(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t
 /* Device pointer to the last result's simplex array (library-owned, valid
  * until the next dt_triangulate or dt_destroy) and its count. */
 DT_API int dt_get_simplices_device(dt_ctx* ctx, const int32_t** dptr, int64_t* count);
+
+/* Neighbourhood update of the merge (Alg. 1, the loop after the merge):
+ * the neighbours of the last result's simplices, as (dim+1) int32 per
+ * simplex in the order of dt_get_simplices.  Entry j of simplex r is the
+ * simplex sharing every vertex of r except its j-th, or -1 when that facet
+ * lies on the convex hull.  Computed on the first call after dt_triangulate
+ * unless dt_config.neighbors made dt_triangulate compute it.  out is host or
+ * device with room for capacity simplices; with out == NULL only *count is
+ * written.  DT_E_ARG after a batched call (no single result) or when
+ * capacity is too small. */
+DT_API int dt_get_neighbors(dt_ctx* ctx, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Certify that m simplices (dim+1 int32 vertex indices each, any order
+ * within a row, host or device) are the Delaunay triangulation of the n
+ * points (row-major float64, host or device) under the same perturbation
+ * rule as dt_triangulate; the checks are listed with dt_validation.  The
+ * result goes to *out; the call returns DT_OK whether or not the rows pass
+ * (bad indices are counted, not errors).  Errors: DT_E_ARG (null pointers,
+ * dim, n < dim + 1, m < 0), DT_E_NOMEM, DT_E_RANGE, DT_E_OVERFLOW, DT_E_CUDA.
+ * The context's last triangulation result is left untouched. */
+DT_API int dt_validate(dt_ctx* ctx, const double* points, int64_t n, int dim, const int32_t* simplices,
+                       int64_t m, dt_validation* out);
 
 /* Statistics of the last call. */
 DT_API int dt_get_stats(dt_ctx* ctx, dt_stats* stats);

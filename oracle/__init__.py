@@ -14,6 +14,8 @@ Contents
   (tiny inputs only): the definition itself.
 * ``predicates`` -- orient / insphere / closer signs on index tuples.
 * ``nearest``    -- exact nearest sample site (Alg. 2, assignment loop).
+* ``neighbors``  -- the neighbour relation of a set of simplices (the state
+  the merge's neighbourhood update must reach).
 * the divide-step references in ``oracle.divide`` (sampling, graph, weights,
   partition invariants, labels, kd median split, border set, merge rule and
   the partition-quality metrics of Sec. 4.6).
@@ -198,6 +200,32 @@ def edges(simplices: np.ndarray) -> np.ndarray:
     pairs = [S[:, [i, j]] for i in range(D1) for j in range(i + 1, D1)]
     e = np.sort(np.concatenate(pairs, axis=0), axis=1)
     return np.unique(e, axis=0)
+
+
+def neighbors(simplices: np.ndarray) -> np.ndarray:
+    """The neighbour relation of a triangulation, by its definition (the
+    neighbourhood update of Alg. 1 must end with it): entry [r, j] is the
+    row sharing every vertex of row r except row r's j-th, -1 when no other
+    row has that facet (a hull facet).  Raises if a facet is in more than
+    two rows."""
+    S = np.asarray(simplices, dtype=np.int64)
+    m, D1 = S.shape if S.ndim == 2 else (0, 1)
+    out = -np.ones((m, D1), dtype=np.int64)
+    if m == 0:
+        return out
+    F = np.concatenate([np.sort(np.delete(S, j, axis=1), axis=1) for j in range(D1)])
+    slot = np.concatenate([np.arange(m) * D1 + j for j in range(D1)])
+    order = np.lexsort(F.T[::-1])
+    F, slot = F[order], slot[order]
+    same = np.all(F[1:] == F[:-1], axis=1)
+    if len(same) > 1:
+        assert not np.any(same[1:] & same[:-1]), "a facet lies in more than two simplices"
+    i = np.nonzero(same)[0]
+    a, b = slot[i], slot[i + 1]
+    flat = out.reshape(-1)
+    flat[a] = b // D1
+    flat[b] = a // D1
+    return out
 
 
 def hull_vertex_count(simplices: np.ndarray) -> int:

@@ -47,7 +47,8 @@ class Config(ctypes.Structure):
                 ("lp_rounds", ctypes.c_int), ("epsilon", ctypes.c_double),
                 ("grid_cell", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("base_threshold", ctypes.c_int), ("validate", ctypes.c_int),
-                ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class KernelProfile(ctypes.Structure):
@@ -64,7 +65,8 @@ class Stats(ctypes.Structure):
                 ("rounds_max", ctypes.c_int32), ("exact_calls", ctypes.c_int32),
                 ("ms_total", ctypes.c_double), ("ms_phase", ctypes.c_double * 8),
                 ("partition_size_max", ctypes.c_int64), ("partition_size_min", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("hull_facets", ctypes.c_int64), ("validated", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32)]
 
     def as_dict(self):
         d = {}
@@ -72,6 +74,16 @@ class Stats(ctypes.Structure):
             v = getattr(self, name)
             d[name] = list(v) if name == "ms_phase" else v
         return d
+
+
+class Validation(ctypes.Structure):
+    """Result of the Delaunay certificate (dt_validate)."""
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "simplices", "interior_facets", "hull_facets", "edges", "euler", "bad_index", "flat", "non_manifold",
+        "asymmetric", "folded", "non_delaunay", "non_convex", "unused_points", "pivot_limit", "violations")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lib = None
@@ -116,6 +128,8 @@ def load_library(build: bool = True):
         "dt_get_batch_simplices": ([p, p, i64, p, p], i32),
         "dt_get_batch_status": ([p, p, i32], i32),
         "dt_select_sample_noalloc": ([i32, p, i64, i64, ctypes.c_uint64, p], i32),
+        "dt_get_neighbors": ([p, p, i64, p], i32),
+        "dt_validate": ([p, p, i64, i32, p, i64, p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -240,6 +254,28 @@ class Triangulator:
             out = np.empty((cnt.value, s.dim + 1), dtype=np.int32)
         self._check(self.L.dt_get_simplices(self.ctx, _ptr(out), cnt.value, ctypes.byref(cnt)))
         return out
+
+    def neighbors(self, out=None):
+        """Neighbour array of the last result (the merge's neighbourhood
+        update): row r, column j = the simplex opposite vertex j of simplex r,
+        -1 on the convex hull; rows in the order of simplices()."""
+        cnt = ctypes.c_int64()
+        self._check(self.L.dt_get_neighbors(self.ctx, None, 0, ctypes.byref(cnt)))
+        if out is None:
+            out = np.empty((cnt.value, self.stats().dim + 1), dtype=np.int32)
+        self._check(self.L.dt_get_neighbors(self.ctx, _ptr(out), cnt.value, ctypes.byref(cnt)))
+        return out
+
+    def validate(self, points, simplices) -> dict:
+        """Certificate that `simplices` is the Delaunay triangulation of
+        `points` (see Validation); returns the counters as a dict."""
+        P, n, dim = _as_points(points)
+        S = simplices
+        if not hasattr(S, "data_ptr"):
+            S = np.ascontiguousarray(S, dtype=np.int32).reshape(-1, dim + 1)
+        v = Validation()
+        self._check(self.L.dt_validate(self.ctx, _ptr(P), n, dim, _ptr(S), len(S), ctypes.byref(v)))
+        return v.as_dict()
 
     def simplex_count(self) -> int:
         cnt = ctypes.c_int64()

@@ -29,9 +29,11 @@ __device__ __forceinline__ int inst_of_slot(const int* toff, int ninst, int s) {
 
 // Every live finite simplex in the used part of each instance's arena,
 // mapped to global indices and sorted; keep (optional, per slot) filters.
+// src (optional) receives, per row, the slot it came from plus src_base.
 template <int D>
 __global__ void k_collect_finite(const int4* tv, const int* toff, const int* tcount, int ninst, int nslots,
-                                 const int* gid, const unsigned char* flag, int mode, int4* rows, int* nrows) {
+                                 const int* gid, const unsigned char* flag, int mode, int4* rows, int* nrows,
+                                 int* src, int src_base) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   bool take = false;
   int4 r = make_int4(0, 0, 0, 0);
@@ -54,7 +56,11 @@ __global__ void k_collect_finite(const int4* tv, const int* toff, const int* tco
   int lane = threadIdx.x & 31, leader = __ffs(mask) - 1, base = 0;
   if (lane == leader) base = atomicAdd(nrows, __popc(mask));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (take) rows[base + __popc(mask & ((1u << lane) - 1))] = r;
+  if (take) {
+    int pos = base + __popc(mask & ((1u << lane) - 1));
+    rows[pos] = r;
+    if (src) src[pos] = s + src_base;
+  }
 }
 
 __global__ void k_bucket_count(const int4* rows, int64_t nrows, int* bucket_count) {
@@ -62,12 +68,15 @@ __global__ void k_bucket_count(const int4* rows, int64_t nrows, int* bucket_coun
   if (i < nrows) atomicAdd(&bucket_count[rows[i].x], 1);
 }
 
-__global__ void k_bucket_scatter(const int4* rows, int64_t nrows, const int* bstart, int* bfill, int4* out) {
+// Scatter into buckets; the payload (optional) travels with its row.
+__global__ void k_bucket_scatter(const int4* rows, const int* pay, int64_t nrows, const int* bstart, int* bfill,
+                                 int4* out, int* pay_out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nrows) return;
   int4 r = rows[i];
   int pos = bstart[r.x] + atomicAdd(&bfill[r.x], 1);
   out[pos] = r;
+  if (pay) pay_out[pos] = pay[i];
 }
 
 __device__ __forceinline__ bool row_less(const int4& a, const int4& b) {
@@ -77,15 +86,21 @@ __device__ __forceinline__ bool row_less(const int4& a, const int4& b) {
 }
 
 template <int D>
-__global__ void k_bucket_sort(int4* rows, const int* bstart, const int* bcount, int64_t nb, int32_t* out) {
+__global__ void k_bucket_sort(int4* rows, int* pay, const int* bstart, const int* bcount, int64_t nb, int32_t* out) {
   int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= nb) return;
   int s = bstart[b], m = bcount[b];
   for (int i = 1; i < m; i++) {
     int4 x = rows[s + i];
+    int px = pay ? pay[s + i] : 0;
     int j = i - 1;
-    while (j >= 0 && row_less(x, rows[s + j])) { rows[s + j + 1] = rows[s + j]; j--; }
+    while (j >= 0 && row_less(x, rows[s + j])) {
+      rows[s + j + 1] = rows[s + j];
+      if (pay) pay[s + j + 1] = pay[s + j];
+      j--;
+    }
     rows[s + j + 1] = x;
+    if (pay) pay[s + j + 1] = px;
   }
   for (int i = 0; i < m; i++) {
     int4 x = rows[s + i];
@@ -97,8 +112,10 @@ __global__ void k_bucket_sort(int4* rows, const int* bstart, const int* bcount, 
 
 // rows: unsorted canonical tuples (sorted within each row); nbuckets > every
 // vertex id.  Writes *out (device, pool-owned) with nrows*(dim+1) int32.
+// src (optional): a payload per input row; *src_out then receives the
+// payload of each output row, in output order (pool-owned).
 int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64_t nbuckets, int32_t** out,
-                      int64_t* nout, const std::string& tag) {
+                      int64_t* nout, const std::string& tag, const int* src, int** src_out) {
   cudaStream_t s = c->stream;
   *nout = nrows;
   int32_t* o = (int32_t*)pool_get(c, tag + ".out", sizeof(int32_t) * (dim + 1) * std::max<int64_t>(nrows, 1));
@@ -106,8 +123,10 @@ int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64
   int* bs = (int*)pool_get(c, "canon.bs", 4 * nbuckets);
   int* bf = (int*)pool_get(c, "canon.bf", 4 * nbuckets);
   int4* tmp = (int4*)pool_get(c, "canon.tmp", 16 * std::max<int64_t>(nrows, 1));
-  if (!o || !bc || !bs || !bf || !tmp) return set_err(c, DT_E_NOMEM, "canonicalise buffers");
+  int* pay = src ? (int*)pool_get(c, tag + ".src", 4 * std::max<int64_t>(nrows, 1)) : nullptr;
+  if (!o || !bc || !bs || !bf || !tmp || (src && !pay)) return set_err(c, DT_E_NOMEM, "canonicalise buffers");
   *out = o;
+  if (src_out) *src_out = pay;
   if (nrows == 0) return 0;
   CUDA_OK(cudaMemsetAsync(bc, 0, 4 * nbuckets, s));
   CUDA_OK(cudaMemsetAsync(bf, 0, 4 * nbuckets, s));
@@ -115,18 +134,19 @@ int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64
   k_bucket_count<<<g, 256, (++c->launches, 0), s>>>(rows, nrows, bc);
   int rc = exclusive_scan_i32(c, bc, bs, nbuckets, nullptr);
   if (rc) return rc;
-  k_bucket_scatter<<<g, 256, (++c->launches, 0), s>>>(rows, nrows, bs, bf, tmp);
+  k_bucket_scatter<<<g, 256, (++c->launches, 0), s>>>(rows, src, nrows, bs, bf, tmp, pay);
   unsigned gb = (unsigned)ceil_div<int64_t>(nbuckets, 128);
-  if (dim == 2) k_bucket_sort<2><<<gb, 128, (++c->launches, 0), s>>>(tmp, bs, bc, nbuckets, o);
-  else k_bucket_sort<3><<<gb, 128, (++c->launches, 0), s>>>(tmp, bs, bc, nbuckets, o);
+  if (dim == 2) k_bucket_sort<2><<<gb, 128, (++c->launches, 0), s>>>(tmp, pay, bs, bc, nbuckets, o);
+  else k_bucket_sort<3><<<gb, 128, (++c->launches, 0), s>>>(tmp, pay, bs, bc, nbuckets, o);
   return 0;
 }
 
 // Collect the finite live simplices of an engine run as canonical rows in
 // *rows (pool-owned), count in *nrows.  mode 0: all; 1: slots not flagged;
 // 2: flagged slots only.
+// src (optional) receives the pool-owned per-row source slot (+ src_base).
 int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsigned char* flag, int mode,
-                   int4** rows, int64_t* nrows, const std::string& tag) {
+                   int4** rows, int64_t* nrows, const std::string& tag, int** src, int src_base) {
   cudaStream_t s = c->stream;
   int64_t ns = run.total_slots;
   int4* r = (int4*)pool_get(c, tag + ".rows", 16 * std::max<int64_t>(ns / 4, 16));
@@ -137,15 +157,17 @@ int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsign
   int64_t used = 0;
   for (int i = 0; i < run.ninst; i++) used += run.h_tcount[i] - run.h_toff[i];
   r = (int4*)pool_get(c, tag + ".rows", 16 * std::max<int64_t>(used, 16));
-  if (!r) return set_err(c, DT_E_NOMEM, "collect rows");
+  int* sr = src ? (int*)pool_get(c, tag + ".slot", 4 * std::max<int64_t>(used, 16)) : nullptr;
+  if (!r || (src && !sr)) return set_err(c, DT_E_NOMEM, "collect rows");
+  if (src) *src = sr;
   unsigned g = (unsigned)ceil_div<int64_t>(ns, 256);
   if (mode && !flag) mode = 0;
   if (run.dim == 2)
     k_collect_finite<2><<<g, 256, (++c->launches, 0), s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
-                                          flag, mode, r, cnt);
+                                          flag, mode, r, cnt, sr, src_base);
   else
     k_collect_finite<3><<<g, 256, (++c->launches, 0), s>>>((const int4*)run.tv, run.toff, run.tcount, run.ninst, (int)ns, gid,
-                                          flag, mode, r, cnt);
+                                          flag, mode, r, cnt, sr, src_base);
   int h = 0;
   CUDA_OK(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "adjacency.cuh"
 #include "pipeline.cuh"
 
 using namespace gdt;
@@ -331,6 +332,50 @@ extern "C" int dt_get_simplices_device(dt_ctx* c, const int32_t** dptr, int64_t*
   return DT_OK;
 }
 
+// Neighbourhood update of the merge (see include/dt.h).
+extern "C" int dt_get_neighbors(dt_ctx* c, int32_t* out, int64_t capacity, int64_t* count) {
+  if (!c || !count) return DT_E_ARG;
+  if (!c->links_ok) return set_err(c, DT_E_ARG, "no single triangulation result (call dt_triangulate first)");
+  *count = c->nout;
+  if (!out) return DT_OK;
+  if (capacity < c->nout) return set_err(c, DT_E_ARG, "capacity too small");
+  if (cudaSetDevice(c->device) != cudaSuccess) { cudaGetLastError(); return set_err(c, DT_E_CUDA, "cudaSetDevice"); }
+  int rc = ensure_neighbors(c);
+  if (rc) return rc;
+  return copy_out(c, out, c->nbr, sizeof(int32_t) * (c->dim + 1) * c->nout);
+}
+
+// Certificate of a caller's triangulation (see include/dt.h).
+extern "C" int dt_validate(dt_ctx* c, const double* points, int64_t n, int dim, const int32_t* simplices, int64_t m,
+                           dt_validation* out) {
+  if (!c) return DT_E_ARG;
+  if (!points || !out || (dim != 2 && dim != 3) || n < dim + 1 || m < 0 || (m > 0 && !simplices))
+    return set_err(c, DT_E_ARG, "bad validation arguments");
+  if (n >= (int64_t(1) << 28)) return set_err(c, DT_E_ARG, "n must be below 2^28");
+  if (cudaSetDevice(c->device) != cudaSuccess) { cudaGetLastError(); return set_err(c, DT_E_CUDA, "cudaSetDevice"); }
+  void* P = nullptr;
+  int rc = stage_points(c, points, n, dim, &P, "val.in");
+  if (rc) return rc;
+  const int32_t* in = m ? (const int32_t*)stage_in(c, simplices, sizeof(int32_t) * (dim + 1) * m, "val.rows_in", &rc)
+                        : nullptr;
+  if (rc) return rc;
+  int32_t* rows = (int32_t*)pool_get(c, "val.rows", sizeof(int32_t) * (dim + 1) * std::max<int64_t>(m, 1));
+  if (!rows) return set_err(c, DT_E_NOMEM, "validation rows");
+  int64_t bad = 0, nm = 0;
+  rc = prepare_rows(c, dim, in, m, n, rows, &bad);
+  if (rc) return rc;
+  int32_t* nbr = nullptr;
+  rc = match_all_facets(c, dim, rows, m, &nbr, &nm);
+  if (rc) return rc;
+  rc = validate_rows(c, dim, P, n, rows, m, nbr, nm, out);
+  if (rc) return rc;
+  out->bad_index = bad;
+  out->violations += bad;
+  // the neighbour buffer is shared with the last result's: recompute it on demand
+  c->nbr_ok = false;
+  return DT_OK;
+}
+
 extern "C" int dt_get_stats(dt_ctx* c, dt_stats* s) {
   if (!c || !s) return DT_E_ARG;
   *s = c->stats;
@@ -368,8 +413,8 @@ extern "C" int dt_get_border_vertices(dt_ctx* c, int32_t* out, int64_t capacity,
 // ---------------------------------------------------------------- predicates entry
 namespace gdt {
 template <int D>
-__global__ void k_eval_pred(const typename PT<D>::T* P, const int* gid, int kind, const int32_t* tup, int64_t m,
-                            int npts, int8_t* out, int* bad) {
+__global__ void k_eval_pred(const typename PT<D>::T* P, const float4* X, const int* gid, int kind, const int32_t* tup,
+                            int64_t m, int npts, int8_t* out, int* bad) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= m) return;
   int w = kind == 0 ? D + 1 : (kind == 3 ? 3 : D + 2);
@@ -380,16 +425,18 @@ __global__ void k_eval_pred(const typename PT<D>::T* P, const int* gid, int kind
   }
   int s = 0;
   if (kind == 0) {
-    s = orient_p(P, t);
+    s = orient_px(P, X, t);
   } else if (kind == 1) {
     int v[4] = {t[0], t[1], t[2], t[3]};
-    int o = orient_p(P, v);
+    int o = orient_px(P, X, v);
     if (o == 0) { out[r] = 0; return; }
     if (o < 0) { int x = v[0]; v[0] = v[1]; v[1] = x; }
-    s = insphere_sos(P, gid, v, t[D + 1], D);
+    s = insphere_sos_x(P, X, gid, v, t[D + 1], D);
   } else if (kind == 2) {
     int v[4] = {t[0], t[1], t[2], t[3]};
-    s = insphere_raw_p(P, v, t[D + 1]);
+    // the sign of the raw determinant (both stages evaluate the same one)
+    s = insphere_f_p(P, X, v, t[D + 1]);
+    if (!s) s = insphere_raw_p(P, v, t[D + 1]);
   } else {
     s = closer(P[t[0]], P[t[1]], P[t[2]], D);
   }
@@ -440,13 +487,17 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
   unsigned long long* ctr = (unsigned long long*)pool_get(c, "pred.ctr", 64);
   if (!ctr) return set_err(c, DT_E_NOMEM, "predicate counters");
   k_read_pred_counters_capi<<<1, 1, (++c->launches, 0), c->stream>>>(ctr + 2, (int*)(ctr + 3));
-  if (dim == 2) {
-    k_pack_points<2><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double2*)P, flags);
-    k_eval_pred<2><<<gm, 128, (++c->launches, 0), c->stream>>>((const double2*)P, g32, kind, tup, m, (int)n, o, flags + 1);
-  } else {
-    k_pack_points<3><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double4_32a*)P, flags);
-    k_eval_pred<3><<<gm, 128, (++c->launches, 0), c->stream>>>((const double4_32a*)P, g32, kind, tup, m, (int)n, o, flags + 1);
-  }
+  if (dim == 2) k_pack_points<2><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double2*)P, flags);
+  else k_pack_points<3><<<g, 256, (++c->launches, 0), c->stream>>>(src, n, (double4_32a*)P, flags);
+  float4* X = nullptr;
+  std::vector<unsigned long long> hu;
+  rc = fp32_points(c, dim, P, nullptr, n, 1, "pred.xs", &X, &hu);
+  if (rc) return rc;
+  if (dim == 2)
+    k_eval_pred<2><<<gm, 128, (++c->launches, 0), c->stream>>>((const double2*)P, X, g32, kind, tup, m, (int)n, o, flags + 1);
+  else
+    k_eval_pred<3><<<gm, 128, (++c->launches, 0), c->stream>>>((const double4_32a*)P, X, g32, kind, tup, m, (int)n, o,
+                                                               flags + 1);
   k_read_pred_counters_capi<<<1, 1, (++c->launches, 0), c->stream>>>(ctr, (int*)(ctr + 1));
   int h[2];
   unsigned long long hc[4];

@@ -40,6 +40,11 @@ struct dt_ctx {
   int32_t* border_vtx = nullptr;         // |V_B| global ids, ascending
   int64_t n_border = 0;
   gdt::EngineRun run_sample, run_parts, run_border;
+  // provenance of the output rows (neighbourhood update) and its result
+  gdt::LinkSources links;
+  bool links_ok = false;
+  int32_t* nbr = nullptr;                // device, (dim+1) per output row
+  bool nbr_ok = false;
   // batched call: per-instance row offsets (count+1) and status
   std::vector<int64_t> batch_offsets;
   std::vector<int> batch_status;
@@ -66,6 +71,10 @@ int exclusive_scan_i64(dt_ctx* c, const long long* in, long long* out, int64_t n
 // Accumulates a per-kernel profile entry (profile mode).
 void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops);
 
+// FP32 copies of the points for the first predicate stage (engine.cu).
+int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t npts, int ninst, const std::string& tag,
+                float4** xs_out, std::vector<unsigned long long>* hu_out);
+
 // Engine (engine.cu).
 int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,
                int64_t npts, const std::vector<int64_t>& poff, const std::string& tag);
@@ -74,8 +83,9 @@ int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* g
 // selected: output rows (sorted gid tuples, lexicographic) into *out.
 // keep (optional, per slot) filters simplices.
 int canonicalize_rows(dt_ctx* c, int dim, const int4* rows, int64_t nrows, int64_t nbuckets,
-                      int32_t** out, int64_t* nout, const std::string& tag);
+                      int32_t** out, int64_t* nout, const std::string& tag, const int* src = nullptr,
+                      int** src_out = nullptr);
 int collect_finite(dt_ctx* c, const EngineRun& run, const int* gid, const unsigned char* flag, int mode,
-                   int4** rows, int64_t* nrows, const std::string& tag);
+                   int4** rows, int64_t* nrows, const std::string& tag, int** src = nullptr, int src_base = 0);
 
 }  // namespace gdt

@@ -1,5 +1,6 @@
 // engine.cu -- batched parallel Bowyer-Watson insertion (see engine.cuh).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -91,7 +92,7 @@ __device__ __forceinline__ int inst_of_slot_e(const TriView<D>& T, int s) {
 template <int D>
 __device__ __forceinline__ int orient_tuple(const TriView<D>& T, const int4& v) {
   int t[4] = {v.x, v.y, v.z, v.w};
-  return orient_p(T.pts, t);
+  return orient_px(T.pts, T.xs, t);
 }
 
 // ---------------------------------------------------------------- init
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
               bad = true;
             } else {
               int vt[4] = {vv.x, vv.y, vv.z, vv.w};
-              if (in_conflict(T.pts, T.gid, vt, p)) {
+              if (in_conflict_x(T.pts, T.xs, T.gid, vt, p, D)) {
                 unsigned long long o = atomicMax(&T.claimC[u], key);
                 if (o > key) {
                   lost = true;
@@ -537,7 +538,9 @@ __global__ void __launch_bounds__(128, 8) k_activate(TriView<D> T, const int* li
     }
     for (int hop = 0; hop < (1 << 20) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
       s = nb_simplex(*comp_ptr(T.tn, s, 0));
-    int r = walk_to(T, s, p, 1 << 22);
+    int steps = 0;
+    int r = walk_to(T, s, p, 1 << 22, &steps);
+    if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
     if (r < 0) {
       set_error(T.st, DT_E_TIMEOUT, 4);
     } else {
@@ -598,6 +601,7 @@ __global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* 
   atomicMax(&T.claimC[r], mkkey(next_round, p));
   // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
   if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
+  if (T.dbg) { atomicAdd(&T.dbg[0], (unsigned long long)steps); atomicMax(&T.dbg[1], (unsigned long long)steps); }
 }
 
 __device__ __forceinline__ unsigned long long ord_key(double x) {
@@ -609,15 +613,27 @@ __global__ void k_ubox_init(unsigned long long* ub, int ninst) {
   if (i < 6 * ninst) ub[i] = (i % 6) < 3 ? ~0ull : 0ull;
 }
 template <int D>
-__global__ void k_inst_bbox(TriView<D> T, int64_t npts, unsigned long long* ub) {
+__global__ void k_inst_bbox(const typename PT<D>::T* pts, const int* pinst, int64_t npts, unsigned long long* ub) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npts) return;
-  int i = T.pinst[p];
+  int i = pinst ? pinst[p] : 0;
   for (int c = 0; c < D; c++) {
-    unsigned long long k = ord_key(comp(T.pts[p], c));
+    unsigned long long k = ord_key(comp(pts[p], c));
     atomicMin(&ub[6 * i + c], k);
     atomicMax(&ub[6 * i + 3 + c], k);
   }
+}
+
+// FP32 copies for the first predicate stage: X = fl32(x - o_i), w = eta_i
+// (xo: per instance the origin (3) and eta (1)).
+template <int D>
+__global__ void k_make_x32(const typename PT<D>::T* pts, const int* pinst, int64_t npts, const double* xo, float4* xs) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const double* o = xo + 4 * (pinst ? pinst[p] : 0);
+  const typename PT<D>::T q = pts[p];
+  xs[p] = make_float4((float)(cx(q) - o[0]), (float)(cy(q) - o[1]), D == 3 ? (float)(cz(q) - o[2]) : 0.0f,
+                      (float)o[3]);
 }
 
 __global__ void k_scatter_levels(const int* level, const int* rank, const int* loff, int64_t n, int* list) {
@@ -664,6 +680,51 @@ int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool 
   CUDA_OK(cudaStreamSynchronize(c->stream));
   *calls = h[0];
   *range = (int)(h[1] & 0xffffffff);
+  return 0;
+}
+
+// FP32 copies of the points for the first predicate stage (see
+// predicates.cuh): per instance (pinst, or one instance when null) the
+// bounding box gives the origin o (its centre) and eta = 2 (u32 + 2 u64) R
+// rounded up, R the largest |x_c - o_c|.  *hu_out receives the boxes as
+// orderable keys (lo[3], hi[3] per instance).
+int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t npts, int ninst, const std::string& tag,
+                float4** xs_out, std::vector<unsigned long long>* hu_out) {
+  cudaStream_t s = c->stream;
+  float4* xs = (float4*)pool_get(c, tag, 16 * (size_t)std::max<int64_t>(npts, 1));
+  double* xo = (double*)pool_get(c, tag + ".o", 8 * 4 * (size_t)ninst);
+  unsigned long long* ub = (unsigned long long*)pool_get(c, tag + ".box", 8 * 6 * (size_t)ninst);
+  if (!xs || !xo || !ub) return set_err(c, DT_E_NOMEM, "fp32 points");
+  *xs_out = xs;
+  std::vector<unsigned long long>& hu = *hu_out;
+  hu.assign(6 * (size_t)ninst, 0);
+  if (npts == 0) return 0;
+  unsigned g = (unsigned)ceil_div<int64_t>(npts, 256);
+  k_ubox_init<<<ceil_div(6 * ninst, 128), 128, (++c->launches, 0), s>>>(ub, ninst);
+  if (dim == 2) k_inst_bbox<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)pts, pinst, npts, ub);
+  else k_inst_bbox<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)pts, pinst, npts, ub);
+  CUDA_OK(cudaMemcpyAsync(hu.data(), ub, 8 * 6 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  std::vector<double> hxo(4 * (size_t)ninst, 0.0);
+  for (int i = 0; i < ninst; i++) {
+    if (hu[6 * i] == ~0ull) continue;   // no points
+    double R = 0.0;
+    for (int cc = 0; cc < dim; cc++) {
+      double lo = host_from_orderable(hu[6 * i + cc]), hi = host_from_orderable(hu[6 * i + 3 + cc]);
+      double o = 0.5 * lo + 0.5 * hi;
+      hxo[4 * i + cc] = o;
+      R = std::max(R, std::max(hi - o, o - lo));
+    }
+    // eta >= 2 (u32 + 2 u64) R, with slack for the roundings of this line
+    double eta = 2.02 * (std::ldexp(1.0, -24) + std::ldexp(1.0, -52)) * R * (1.0 + 1e-9);
+    float ef = (float)eta;
+    if (!((double)ef >= eta)) ef = std::nextafter(ef, INFINITY);
+    hxo[4 * i + 3] = (double)ef;
+  }
+  CUDA_OK(cudaMemcpyAsync(xo, hxo.data(), 8 * 4 * (size_t)ninst, cudaMemcpyHostToDevice, s));
+  if (dim == 2) k_make_x32<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)pts, pinst, npts, xo, xs);
+  else k_make_x32<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)pts, pinst, npts, xo, xs);
+  CUDA_OK(cudaStreamSynchronize(s));   // hxo goes out of scope
   return 0;
 }
 
@@ -736,6 +797,12 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     T.nslots = (int)total;
     T.npts = (int)npts;
     T.prof = nullptr;
+    T.dbg = nullptr;
+    if (getenv("GDT_DEBUG")) {
+      T.dbg = (unsigned long long*)pool_get(c, "eng.dbg", 64);
+      if (!T.dbg) return set_err(c, DT_E_NOMEM, "debug counters");
+      CUDA_OK(cudaMemsetAsync(T.dbg, 0, 64, s));
+    }
     unsigned long long* profc = nullptr;
     if (c->cfg.profile) {
       profc = (unsigned long long*)pool_get(c, "eng.prof", 64);
@@ -744,21 +811,21 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       T.prof = profc;
     }
 
+    // per-instance bounding boxes: origins and error bounds of the FP32
+    // predicate stage, and the hint grids
+    std::vector<unsigned long long> hu;
+    float4* xs = nullptr;
+    { int rc0 = fp32_points(c, D, pts, pinst, npts, ninst, "eng.xs", &xs, &hu); if (rc0) return rc0; }
+    T.xs = xs;
     k_init<D><<<ceil_div(ninst, 64), 64, (++c->launches, 0), s>>>(T, ninst, dpoff, run.toff, run.inst_status);
     T.toff = run.toff;
     T.ninst = ninst;
     T.hint = nullptr;
     if (npts > 0 && !getenv("GDT_NOHINT")) {
-      // per-instance bounding boxes -> grids of about n_i / 4 cells
-      unsigned long long* ub = (unsigned long long*)pool_get(c, "eng.ubox", 8 * 6 * (size_t)ninst);
+      // grids of about n_i / 4 cells
       double* glo = (double*)pool_get(c, tag + ".glo", 8 * 6 * (size_t)ninst);
       int* gdim = (int*)pool_get(c, tag + ".gdim", 4 * 4 * (size_t)ninst);
-      if (!ub || !glo || !gdim) return set_err(c, DT_E_NOMEM, "hint grids");
-      k_ubox_init<<<ceil_div(6 * ninst, 128), 128, (++c->launches, 0), s>>>(ub, ninst);
-      k_inst_bbox<D><<<(unsigned)ceil_div<int64_t>(npts, 256), 256, (++c->launches, 0), s>>>(T, npts, ub);
-      std::vector<unsigned long long> hu(6 * (size_t)ninst);
-      CUDA_OK(cudaMemcpyAsync(hu.data(), ub, 8 * 6 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
-      CUDA_OK(cudaStreamSynchronize(s));
+      if (!glo || !gdim) return set_err(c, DT_E_NOMEM, "hint grids");
       std::vector<double> hg(6 * (size_t)ninst, 0.0);
       std::vector<int> hd(4 * (size_t)ninst, 1);
       int64_t cells = 0;
@@ -904,9 +971,13 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       if (prof) cudaEventRecord(c->pev[5], s);
       if (getenv("GDT_DEBUG")) {
         int hc[5];
+        unsigned long long hd[4];
         cudaMemcpyAsync(hc, cnt, 20, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hd, T.dbg, 32, cudaMemcpyDeviceToHost, s);
+        cudaMemsetAsync(T.dbg, 0, 32, s);
         cudaStreamSynchronize(s);
-        fprintf(stderr, "round %u nact %d cand %d win %d walk %d\n", round, hc[0], hc[2], hc[3], hc[4]);
+        fprintf(stderr, "round %u nact %d cand %d win %d walk %d steps %llu max %llu act_steps %llu act_max %llu\n",
+                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3]);
       }
       k_move_count<<<1, 1, (++c->launches, 0), s>>>(cnt + 0, cnt + 1);
       std::swap(ain, aout);

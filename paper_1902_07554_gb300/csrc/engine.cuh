@@ -33,6 +33,7 @@ template <int D>
 struct TriView {
   using P = typename PT<D>::T;
   const P* pts;             // points (all instances, concatenated)
+  const float4* xs;         // FP32 copies relative to the instance origin; w = error bound eta
   const int* gid;           // global index of each point (perturbation rank)
   const int* pinst;         // instance of each point
   int4* tv;                 // simplex vertex tuples (D+1 used)
@@ -55,6 +56,7 @@ struct TriView {
   const int* gdim;          // per instance: cells per axis (3) and first cell (1)
   const int* toff;          // per instance: first simplex slot
   int ninst;
+  unsigned long long* dbg;  // walk statistics (debug runs only; null otherwise)
 };
 
 struct CandScratch {
@@ -85,6 +87,20 @@ struct EngineRun {
   int* toff = nullptr;
   int* tend = nullptr;
   int* inst_status = nullptr;
+};
+
+// Where each output row came from: a slot of the first arena (partial or
+// direct triangulation), or base1 + a slot of the second (border) arena.
+struct LinkSources {
+  const int4* tv0 = nullptr;
+  const int4* tn0 = nullptr;
+  const int* gid0 = nullptr;
+  int64_t base1 = 0;
+  const int4* tv1 = nullptr;
+  const int4* tn1 = nullptr;
+  const int* gid1 = nullptr;
+  int64_t total = 0;            // base1 + slots of the second arena
+  const int* origin = nullptr;  // per output row
 };
 
 }  // namespace gdt

@@ -41,9 +41,11 @@ __device__ __forceinline__ bool hash_find(const int4* rows, const int* table, un
 }
 
 // Select the simplices of T_B that enter T; append them to out.
+// tbsrc/out_src (optional): the source slot of each row travels with it.
 template <int D>
-__global__ void k_merge_select(const int4* tb, int64_t ntb, const int* label_by_gid, const int4* brows,
-                               const int* table, unsigned mask, int4* out, int* nout) {
+__global__ void k_merge_select(const int4* tb, const int* tbsrc, int64_t ntb, const int* label_by_gid,
+                               const int4* brows, const int* table, unsigned mask, int4* out, int* out_src,
+                               int* nout) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool keep = false;
   int4 r = make_int4(0, 0, 0, 0);
@@ -58,41 +60,56 @@ __global__ void k_merge_select(const int4* tb, int64_t ntb, const int* label_by_
   int lane = threadIdx.x & 31, leader = __ffs(m) - 1, base = 0;
   if (lane == leader) base = atomicAdd(nout, __popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (keep) out[base + __popc(m & ((1u << lane) - 1))] = r;
+  if (keep) {
+    int pos = base + __popc(m & ((1u << lane) - 1));
+    out[pos] = r;
+    if (out_src) out_src[pos] = tbsrc[i];
+  }
 }
 
 int merge(dt_ctx* c, int dim, const EngineRun& parts, const int* gid_sorted, const unsigned char* bflag,
           const EngineRun& border, const int* gid_border, const int* label_by_gid, int4** rows_out,
-          int64_t* nrows_out, MergeStats* ms) {
+          int64_t* nrows_out, MergeStats* ms, int** src_out) {
   cudaStream_t s = c->stream;
   int4 *brows, *tbrows, *trows;
+  int *tbsrc = nullptr, *tsrc = nullptr;
   int64_t nb, ntb, nt;
+  const bool want_src = src_out != nullptr;
   int rc = collect_finite(c, parts, gid_sorted, bflag, 2, &brows, &nb, "m.B");
   if (rc) return rc;
-  rc = collect_finite(c, border, gid_border, nullptr, 0, &tbrows, &ntb, "m.TB");
+  rc = collect_finite(c, border, gid_border, nullptr, 0, &tbrows, &ntb, "m.TB", want_src ? &tbsrc : nullptr,
+                      (int)parts.total_slots);
   if (rc) return rc;
-  rc = collect_finite(c, parts, gid_sorted, bflag, 1, &trows, &nt, "m.T");
+  rc = collect_finite(c, parts, gid_sorted, bflag, 1, &trows, &nt, "m.T", want_src ? &tsrc : nullptr, 0);
   if (rc) return rc;
   unsigned tsize = 64;
   while (tsize < 2 * nb + 2) tsize <<= 1;
   int* table = (int*)pool_get(c, "m.table", 4 * (size_t)tsize);
   int* cnt = (int*)pool_get(c, "m.cnt", 16);
   int4* all = (int4*)pool_get(c, "m.all", 16 * (size_t)(nt + ntb + 1));
-  if (!table || !cnt || !all) return set_err(c, DT_E_NOMEM, "merge buffers");
+  int* allsrc = want_src ? (int*)pool_get(c, "m.allsrc", 4 * (size_t)(nt + ntb + 1)) : nullptr;
+  if (!table || !cnt || !all || (want_src && !allsrc)) return set_err(c, DT_E_NOMEM, "merge buffers");
   CUDA_OK(cudaMemsetAsync(table, 0xff, 4 * (size_t)tsize, s));
   CUDA_OK(cudaMemsetAsync(cnt, 0, 16, s));
   if (nb) k_hash_insert<<<(unsigned)ceil_div<int64_t>(nb, 256), 256, (++c->launches, 0), s>>>(brows, nb, table, tsize - 1, cnt + 1);
   if (nt) CUDA_OK(cudaMemcpyAsync(all, trows, 16 * (size_t)nt, cudaMemcpyDeviceToDevice, s));
+  if (nt && want_src) CUDA_OK(cudaMemcpyAsync(allsrc, tsrc, 4 * (size_t)nt, cudaMemcpyDeviceToDevice, s));
   if (ntb) {
     unsigned g = (unsigned)ceil_div<int64_t>(ntb, 256);
-    if (dim == 2) k_merge_select<2><<<g, 256, (++c->launches, 0), s>>>(tbrows, ntb, label_by_gid, brows, table, tsize - 1, all + nt, cnt);
-    else k_merge_select<3><<<g, 256, (++c->launches, 0), s>>>(tbrows, ntb, label_by_gid, brows, table, tsize - 1, all + nt, cnt);
+    int* osrc = want_src ? allsrc + nt : nullptr;
+    if (dim == 2)
+      k_merge_select<2><<<g, 256, (++c->launches, 0), s>>>(tbrows, tbsrc, ntb, label_by_gid, brows, table, tsize - 1,
+                                                           all + nt, osrc, cnt);
+    else
+      k_merge_select<3><<<g, 256, (++c->launches, 0), s>>>(tbrows, tbsrc, ntb, label_by_gid, brows, table, tsize - 1,
+                                                           all + nt, osrc, cnt);
   }
   int h[2];
   CUDA_OK(cudaMemcpyAsync(h, cnt, 8, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
   if (h[1]) return set_err(c, DT_E_OVERFLOW, "border hash table full");
   *rows_out = all;
+  if (want_src) *src_out = allsrc;
   *nrows_out = nt + h[0];
   ms->n_border_simplices = nb;
   ms->n_tb = ntb;

@@ -2,6 +2,7 @@
 // border detection, border DT, merge, canonical output.
 #include <cmath>
 
+#include "adjacency.cuh"
 #include "border.cuh"
 #include "divide.cuh"
 #include "merge.cuh"
@@ -28,10 +29,19 @@ static int run_direct(dt_ctx* c, const void* P, int64_t n, int dim) {
   if (c->run_parts.h_status[0] != 0) return set_err(c, DT_E_ARG, "too few points");
   c->stats.rounds_max = c->run_parts.rounds;
   int4* rows; int64_t nrows;
-  rc = collect_finite(c, c->run_parts, gid, nullptr, 0, &rows, &nrows, "final");
+  int *src, *osrc;
+  rc = collect_finite(c, c->run_parts, gid, nullptr, 0, &rows, &nrows, "final", &src, 0);
   if (rc) return rc;
-  rc = canonicalize_rows(c, dim, rows, nrows, n, &c->out, &c->nout, "final");
+  rc = canonicalize_rows(c, dim, rows, nrows, n, &c->out, &c->nout, "final", src, &osrc);
   if (rc) return rc;
+  c->links = LinkSources();
+  c->links.tv0 = (const int4*)c->run_parts.tv;
+  c->links.tn0 = (const int4*)c->run_parts.tn;
+  c->links.gid0 = gid;
+  c->links.base1 = c->run_parts.total_slots;
+  c->links.total = c->run_parts.total_slots;
+  c->links.origin = osrc;
+  c->links_ok = true;
   c->stats.k = 1;
   c->labels = (int32_t*)pool_get(c, "pl.labels", 4 * n);
   if (!c->labels) return set_err(c, DT_E_NOMEM, "labels");
@@ -191,11 +201,23 @@ static int run_dc(dt_ctx* c, const void* P, int64_t n, int dim, int k, double fr
   int4* rows;
   int64_t nrows;
   MergeStats ms;
-  rc = merge(c, dim, c->run_parts, gid_sorted, bflag, c->run_border, gidB, c->labels, &rows, &nrows, &ms);
+  int *src, *osrc;
+  rc = merge(c, dim, c->run_parts, gid_sorted, bflag, c->run_border, gidB, c->labels, &rows, &nrows, &ms, &src);
   if (rc) return rc;
   cudaEventRecord(c->ev[8], s);
-  rc = canonicalize_rows(c, dim, rows, nrows, n, &c->out, &c->nout, "final");
+  rc = canonicalize_rows(c, dim, rows, nrows, n, &c->out, &c->nout, "final", src, &osrc);
   if (rc) return rc;
+  c->links = LinkSources();
+  c->links.tv0 = (const int4*)c->run_parts.tv;
+  c->links.tn0 = (const int4*)c->run_parts.tn;
+  c->links.gid0 = gid_sorted;
+  c->links.base1 = c->run_parts.total_slots;
+  c->links.tv1 = (const int4*)c->run_border.tv;
+  c->links.tn1 = (const int4*)c->run_border.tn;
+  c->links.gid1 = gidB;
+  c->links.total = c->run_parts.total_slots + c->run_border.total_slots;
+  c->links.origin = osrc;
+  c->links_ok = true;
   cudaEventRecord(c->ev[9], s);
   // border vertex list in global indices, ascending
   unsigned char* fg = (unsigned char*)pool_get(c, "dc.fg", n);
@@ -257,6 +279,8 @@ __global__ void k_rows_to_local(int32_t* rows, int64_t nrows, const long long* o
 // [offsets[i], offsets[i+1]); each is triangulated directly.
 int run_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count, int dim) {
   cudaStream_t s = c->stream;
+  c->links_ok = false;
+  c->nbr_ok = false;
   int64_t n = offsets[count];
   std::vector<int64_t> poff(offsets, offsets + count + 1);
   std::vector<long long> hoff(offsets, offsets + count + 1);
@@ -311,12 +335,48 @@ int run_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count
   return check_status(c, "batch");
 }
 
+// Neighbourhood update of the last result (once per result).
+int ensure_neighbors(dt_ctx* c) {
+  if (c->nbr_ok) return 0;
+  if (!c->links_ok) return set_err(c, DT_E_ARG, "no single triangulation result to link");
+  int rc = neighbor_update(c, c->dim, c->out, c->nout, c->links, &c->nbr);
+  if (rc) return rc;
+  c->nbr_ok = true;
+  return 0;
+}
+
 int run_pipeline(dt_ctx* c, const double* points, int64_t n, int dim, int k, double frac) {
   void* P = nullptr;
+  c->links_ok = false;
+  c->nbr_ok = false;
   int rc = stage_points(c, points, n, dim, &P, "in");
   if (rc) return rc;
-  if (k == 1 || n / k < c->cfg.base_threshold) return run_direct(c, P, n, dim);
-  return run_dc(c, P, n, dim, k, frac);
+  rc = (k == 1 || n / k < c->cfg.base_threshold) ? run_direct(c, P, n, dim) : run_dc(c, P, n, dim, k, frac);
+  if (rc) return rc;
+  if (!c->cfg.neighbors && !c->cfg.validate) return 0;
+  cudaEventRecord(c->ev[10], c->stream);
+  rc = ensure_neighbors(c);
+  if (rc) return rc;
+  if (c->cfg.validate) {
+    dt_validation v;
+    rc = validate_rows(c, dim, P, n, c->out, c->nout, c->nbr, 0, &v);
+    if (rc) return rc;
+    if (v.violations) {
+      char msg[256];
+      snprintf(msg, sizeof msg,
+               "certificate failed: flat %lld, non-manifold %lld, asymmetric %lld, folded %lld, non-Delaunay %lld, "
+               "non-convex %lld, unused %lld, pivot %lld, euler %lld",
+               (long long)v.flat, (long long)v.non_manifold, (long long)v.asymmetric, (long long)v.folded,
+               (long long)v.non_delaunay, (long long)v.non_convex, (long long)v.unused_points,
+               (long long)v.pivot_limit, (long long)v.euler);
+      return set_err(c, DT_E_INTERNAL, msg);
+    }
+    c->stats.validated = 1;
+  }
+  cudaEventRecord(c->ev[11], c->stream);
+  CUDA_OK(cudaEventSynchronize(c->ev[11]));
+  c->stats.ms_phase[7] = ev_ms(c, 10, 11);
+  return 0;
 }
 
 }  // namespace gdt

@@ -8,6 +8,7 @@ int run_pipeline(dt_ctx* c, const double* points, int64_t n, int dim, int k, dou
 int stage_points(dt_ctx* c, const double* points, int64_t n, int dim, void** P_out, const char* tag,
                  const int* inst = nullptr);
 int run_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count, int dim);
+int ensure_neighbors(dt_ctx* c);
 void* stage_in(dt_ctx* c, const void* src, size_t bytes, const std::string& name, int* rc);
 int copy_out(dt_ctx* c, void* dst, const void* src, size_t bytes);
 bool is_device_ptr(const void* p);

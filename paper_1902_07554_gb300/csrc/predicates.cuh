@@ -480,6 +480,111 @@ static __device__ __forceinline__ int insphere3_raw(double4_32a a, double4_32a b
   return s ? s : insphere3_exact(a, b, c, d, q);
 }
 
+// ---------------------------------------------------------------- FP32 stage
+// A first stage in front of the FP64 filter (GB300 issues FP32 at a far
+// higher rate than FP64).  Every point carries X = fl32(fl64(x - o)) for the
+// origin o of its instance and, in X.w, eta >= 2 (u32 + 2 u64) R with R the
+// instance's largest |x_c - o_c| (u32 = 2^-24, u64 = 2^-53).  For two points
+// of one instance the FP32 difference d = fl32(X_a - X_b) then satisfies
+//   |d - d*| <= e(d) = eta + u32 |d| / (1 - u32)
+// against the exact difference d* = x_a - x_b.  Write P for the permanent of
+// a determinant (its monomials in absolute value) and D_i = |d_i| + e(d_i).
+// Monomial by monomial, |det(d*) - det(d)| <= P(D) - P(|d|), and the FP32
+// evaluation of det(d) is off by at most about 45 u32 P(|d|) (the roundings
+// along one monomial); so the sign of the FP32 determinant is the exact sign
+// when |det| > (P(D) - P(|d|)) + F32_C P(D).  F32_C = 1e-5 (about 168 u32)
+// also covers the rounding of both permanents and of the bound itself.  Out
+// of the range (F32_TINY, F32_HUGE), or when nothing is certain, the stage
+// returns 0 and the FP64 filter decides.
+constexpr float F32_C = 1e-5f;
+constexpr float F32_TINY = 1e-25f, F32_HUGE = 1e30f;
+
+static __device__ __forceinline__ float f32_up(float d, float eta) {
+  // |d| + e(d), rounded upwards; 1.2e-7 > u32 / (1 - u32) with room for rounding
+  return __fadd_ru(fabsf(d), __fadd_ru(eta, 1.2e-7f * fabsf(d)));
+}
+static __device__ __forceinline__ int f32_decide(float det, float pd, float p0) {
+  if (!(pd > F32_TINY && pd < F32_HUGE)) return 0;
+  float bound = (pd - p0) + F32_C * pd;
+  if (det > bound) return 1;
+  if (det < -bound) return -1;
+  return 0;
+}
+
+static __device__ __forceinline__ int orient2_f(float4 a, float4 b, float4 c) {
+  const float eta = a.w;
+  float bx = b.x - a.x, by = b.y - a.y, cx_ = c.x - a.x, cy_ = c.y - a.y;
+  float det = bx * cy_ - by * cx_;
+  float p0 = fabsf(bx * cy_) + fabsf(by * cx_);
+  float Bx = f32_up(bx, eta), By = f32_up(by, eta), Cx = f32_up(cx_, eta), Cy = f32_up(cy_, eta);
+  float pd = Bx * Cy + By * Cx;
+  return f32_decide(det, pd, p0);
+}
+
+static __device__ __forceinline__ int orient3_f(float4 a, float4 b, float4 c, float4 d) {
+  const float eta = a.w;
+  float b0 = b.x - a.x, b1 = b.y - a.y, b2 = b.z - a.z;
+  float c0 = c.x - a.x, c1 = c.y - a.y, c2 = c.z - a.z;
+  float d0 = d.x - a.x, d1 = d.y - a.y, d2 = d.z - a.z;
+  float m0 = c1 * d2 - c2 * d1, m1 = c2 * d0 - c0 * d2, m2 = c0 * d1 - c1 * d0;
+  float det = b0 * m0 + b1 * m1 + b2 * m2;
+  float p0 = fabsf(b0) * (fabsf(c1 * d2) + fabsf(c2 * d1)) + fabsf(b1) * (fabsf(c2 * d0) + fabsf(c0 * d2)) +
+             fabsf(b2) * (fabsf(c0 * d1) + fabsf(c1 * d0));
+  float B0 = f32_up(b0, eta), B1 = f32_up(b1, eta), B2 = f32_up(b2, eta);
+  float C0 = f32_up(c0, eta), C1 = f32_up(c1, eta), C2 = f32_up(c2, eta);
+  float D0 = f32_up(d0, eta), D1 = f32_up(d1, eta), D2 = f32_up(d2, eta);
+  float pd = B0 * (C1 * D2 + C2 * D1) + B1 * (C2 * D0 + C0 * D2) + B2 * (C0 * D1 + C1 * D0);
+  return f32_decide(det, pd, p0);
+}
+
+// > 0: q inside the circumcircle of the positively oriented abc (0: undecided)
+static __device__ __forceinline__ int insphere2_f(float4 a, float4 b, float4 c, float4 q) {
+  const float eta = q.w;
+  float ax = a.x - q.x, ay = a.y - q.y, bx = b.x - q.x, by = b.y - q.y, cx_ = c.x - q.x, cy_ = c.y - q.y;
+  float la = ax * ax + ay * ay, lb = bx * bx + by * by, lc = cx_ * cx_ + cy_ * cy_;
+  float det = la * (bx * cy_ - by * cx_) - lb * (ax * cy_ - ay * cx_) + lc * (ax * by - ay * bx);
+  float p0 = la * (fabsf(bx * cy_) + fabsf(by * cx_)) + lb * (fabsf(ax * cy_) + fabsf(ay * cx_)) +
+             lc * (fabsf(ax * by) + fabsf(ay * bx));
+  float Ax = f32_up(ax, eta), Ay = f32_up(ay, eta), Bx = f32_up(bx, eta), By = f32_up(by, eta);
+  float Cx = f32_up(cx_, eta), Cy = f32_up(cy_, eta);
+  float pd = (Ax * Ax + Ay * Ay) * (Bx * Cy + By * Cx) + (Bx * Bx + By * By) * (Ax * Cy + Ay * Cx) +
+             (Cx * Cx + Cy * Cy) * (Ax * By + Ay * Bx);
+  return f32_decide(det, pd, p0);
+}
+
+// > 0: q inside the circumsphere of the positively oriented abcd (0: undecided)
+static __device__ __forceinline__ int insphere3_f(float4 a, float4 b, float4 c, float4 d, float4 q) {
+  const float eta = q.w;
+  float ax = a.x - q.x, ay = a.y - q.y, az = a.z - q.z;
+  float bx = b.x - q.x, by = b.y - q.y, bz = b.z - q.z;
+  float cx_ = c.x - q.x, cy_ = c.y - q.y, cz_ = c.z - q.z;
+  float dx = d.x - q.x, dy = d.y - q.y, dz = d.z - q.z;
+  float la = ax * ax + ay * ay + az * az, lb = bx * bx + by * by + bz * bz;
+  float lc = cx_ * cx_ + cy_ * cy_ + cz_ * cz_, ld = dx * dx + dy * dy + dz * dz;
+  float ab = ax * by - ay * bx, ac = ax * cy_ - ay * cx_, ad = ax * dy - ay * dx;
+  float bc = bx * cy_ - by * cx_, bd = bx * dy - by * dx, cd = cx_ * dy - cy_ * dx;
+  float det = (la * (bz * cd - cz_ * bd + dz * bc) - lb * (az * cd - cz_ * ad + dz * ac)) +
+              (lc * (az * bd - bz * ad + dz * ab) - ld * (az * bc - bz * ac + cz_ * ab));
+  float pab = fabsf(ax * by) + fabsf(ay * bx), pac = fabsf(ax * cy_) + fabsf(ay * cx_);
+  float pad = fabsf(ax * dy) + fabsf(ay * dx), pbc = fabsf(bx * cy_) + fabsf(by * cx_);
+  float pbd = fabsf(bx * dy) + fabsf(by * dx), pcd = fabsf(cx_ * dy) + fabsf(cy_ * dx);
+  float p0 = (la * (fabsf(bz) * pcd + fabsf(cz_) * pbd + fabsf(dz) * pbc) +
+              lb * (fabsf(az) * pcd + fabsf(cz_) * pad + fabsf(dz) * pac)) +
+             (lc * (fabsf(az) * pbd + fabsf(bz) * pad + fabsf(dz) * pab) +
+              ld * (fabsf(az) * pbc + fabsf(bz) * pac + fabsf(cz_) * pab));
+  float Ax = f32_up(ax, eta), Ay = f32_up(ay, eta), Az = f32_up(az, eta);
+  float Bx = f32_up(bx, eta), By = f32_up(by, eta), Bz = f32_up(bz, eta);
+  float Cx = f32_up(cx_, eta), Cy = f32_up(cy_, eta), Cz = f32_up(cz_, eta);
+  float Dx = f32_up(dx, eta), Dy = f32_up(dy, eta), Dz = f32_up(dz, eta);
+  float qab = Ax * By + Ay * Bx, qac = Ax * Cy + Ay * Cx, qad = Ax * Dy + Ay * Dx;
+  float qbc = Bx * Cy + By * Cx, qbd = Bx * Dy + By * Dx, qcd = Cx * Dy + Cy * Dx;
+  float pd = ((Ax * Ax + Ay * Ay + Az * Az) * (Bz * qcd + Cz * qbd + Dz * qbc) +
+              (Bx * Bx + By * By + Bz * Bz) * (Az * qcd + Cz * qad + Dz * qac)) +
+             ((Cx * Cx + Cy * Cy + Cz * Cz) * (Az * qbd + Bz * qad + Dz * qab) +
+              (Dx * Dx + Dy * Dy + Dz * Dz) * (Az * qbc + Bz * qac + Cz * qab));
+  return f32_decide(det, pd, p0);
+}
+
 // ---------------------------------------------------------------- helpers on indices
 static __device__ __forceinline__ int orient_p(const double2* P, const int* v) {
   return orient2(P[v[0]], P[v[1]], P[v[2]]);
@@ -524,6 +629,31 @@ static __device__ __noinline__ int insphere_sos_tail(const P* pts, const int* gi
 template <typename P>
 static __device__ __forceinline__ int insphere_sos(const P* pts, const int* gid, const int* v, int q, int D) {
   int r = insphere_raw_p(pts, v, q);
+  if (r) return r;
+  return insphere_sos_tail(pts, gid, v, q, D);
+}
+
+// The same predicates with the FP32 stage first (X: the points' FP32 copies).
+static __device__ __forceinline__ int orient_px(const double2* P, const float4* X, const int* v) {
+  int s = orient2_f(X[v[0]], X[v[1]], X[v[2]]);
+  return s ? s : orient2(P[v[0]], P[v[1]], P[v[2]]);
+}
+static __device__ __forceinline__ int orient_px(const double4_32a* P, const float4* X, const int* v) {
+  int s = orient3_f(X[v[0]], X[v[1]], X[v[2]], X[v[3]]);
+  return s ? s : orient3(P[v[0]], P[v[1]], P[v[2]], P[v[3]]);
+}
+static __device__ __forceinline__ int insphere_f_p(const double2*, const float4* X, const int* v, int q) {
+  return insphere2_f(X[v[0]], X[v[1]], X[v[2]], X[q]);
+}
+static __device__ __forceinline__ int insphere_f_p(const double4_32a*, const float4* X, const int* v, int q) {
+  return insphere3_f(X[v[0]], X[v[1]], X[v[2]], X[v[3]], X[q]);
+}
+template <typename P>
+static __device__ __forceinline__ int insphere_sos_x(const P* pts, const float4* X, const int* gid, const int* v, int q,
+                                                     int D) {
+  int r = insphere_f_p(pts, X, v, q);
+  if (r) return r;
+  r = insphere_raw_p(pts, v, q);
   if (r) return r;
   return insphere_sos_tail(pts, gid, v, q, D);
 }
@@ -610,6 +740,21 @@ static __device__ __forceinline__ bool in_conflict(const double4_32a* P, const i
   int f[3], k = 0;
   for (int i = 0; i < 4; i++) if (i != g) f[k++] = v[i];
   return ghost_coplanar3(P, gid, f, q);
+}
+
+// in_conflict with the FP32 stage in front of the orientation and insphere tests.
+template <typename P>
+static __device__ __forceinline__ bool in_conflict_x(const P* pts, const float4* X, const int* gid, const int* v, int q,
+                                                     int D) {
+  int g = -1;
+#pragma unroll
+  for (int i = 0; i <= D; i++) if (v[i] == INF_V) g = i;
+  if (g < 0) return insphere_sos_x(pts, X, gid, v, q, D) > 0;
+  int t[4] = {v[0], v[1], v[2], D == 3 ? v[3] : 0};
+  t[g] = q;
+  int o = orient_px(pts, X, t);
+  if (o) return o > 0;
+  return in_conflict(pts, gid, v, q);   // q on the hull facet's hyperplane: exact path
 }
 
 // Exact sign of |p - a|^2 - |p - b|^2 (negative: a is closer).

@@ -48,6 +48,22 @@ def test_predicates_degenerate_and_near_degenerate(tri, D):
     assert tri.stats().exact_calls > 0
 
 
+@pytest.mark.parametrize("D", [2, 3])
+def test_predicates_near_the_fp32_bound(tri, D):
+    """Tuples whose determinants sit near the FP32 stage's error bound:
+    cospherical points moved by relative amounts from 1e-9 to 1e-4, and a
+    tight cluster beside one far outlier (a large eta for every test)."""
+    rng = np.random.default_rng(11 + D)
+    u = rng.normal(size=(300, D))
+    S = 0.3 * u / np.linalg.norm(u, axis=1, keepdims=True) + 0.5
+    S *= 1.0 + 10.0 ** rng.uniform(-9, -4, size=(300, 1)) * rng.choice([-1, 1], size=(300, 1))
+    C = np.concatenate([0.5 + 1e-3 * rng.random((199, D)), np.full((1, D), 900.0)])
+    for P in (S, C):
+        for kind, w in [("orient", D + 1), ("insphere_raw", D + 2), ("insphere", D + 2)]:
+            T = _tuples(rng, len(P) - (P is C), w, 4000)
+            assert np.array_equal(tri.eval_predicates(P, kind, T), oracle.predicates(P, kind, T)), kind
+
+
 def test_predicates_wide_exponent_range(tri):
     P = np.array([[1e-200, 0.0], [1.0, 1e-150], [0.0, 1.0], [1.0, 1.0], [1e100, 1e-100], [3e-5, 7e-9]])
     rng = np.random.default_rng(0)

@@ -278,3 +278,50 @@ def test_nearest_matches_numpy(orc):
     Q2 = np.array([[1.0, 0.0]])
     assert orc.nearest(Q2, S2)[0] == 0
     assert orc.nearest(Q2, S2, np.array([5, 1, 0]))[0] == 1
+
+
+# ---------------------------------------------------------------- neighbour relation
+def py_neighbors(S):
+    """Quadratic definition: rows r, t are neighbours across r's j-th vertex
+    when they share every vertex of r but that one."""
+    S = [list(map(int, r)) for r in S]
+    out = [[-1] * len(r) for r in S]
+    for r, a in enumerate(S):
+        for t, b in enumerate(S):
+            if t == r:
+                continue
+            common = set(a) & set(b)
+            if len(common) == len(a) - 1:
+                j = [x for x in a if x not in common][0]
+                out[r][a.index(j)] = t
+    return np.array(out, dtype=np.int64).reshape(-1, len(S[0]) if S else 1)
+
+
+@pytest.mark.parametrize("D,n,shape", [(2, 40, "uniform"), (2, 36, "grid"), (3, 30, "uniform"), (3, 27, "grid")])
+def test_neighbors_match_quadratic_definition(orc, D, n, shape):
+    P = pointsets.uniform(n, D, 5) if shape == "uniform" else pointsets.grid((6, 6) if D == 2 else (3, 3, 3), seed=5)
+    S = orc.delaunay(P)
+    assert np.array_equal(orc.neighbors(S), py_neighbors(S))
+
+
+@pytest.mark.parametrize("D,n", [(2, 3000), (3, 2000)])
+def test_neighbors_hull_count_and_symmetry(orc, D, n):
+    spatial = pytest.importorskip("scipy.spatial")
+    P = pointsets.uniform(n, D, 77)
+    S = orc.delaunay(P)
+    N = orc.neighbors(S)
+    h = len(spatial.ConvexHull(P).vertices)
+    hull_facets = int((N < 0).sum())
+    assert hull_facets == (h if D == 2 else 2 * h - 4)
+    r, j = np.nonzero(N >= 0)
+    t = N[r, j]
+    assert np.all((N[t] == r[:, None]).sum(axis=1) == 1)      # the link is returned exactly once
+    # the two rows share all but one vertex
+    shared = (S[r][:, :, None] == S[t][:, None, :]).any(axis=2).sum(axis=1)
+    assert np.all(shared == D)
+
+
+def test_neighbors_reject_a_facet_in_three_rows(orc):
+    S = np.array([[0, 1, 2], [0, 1, 3], [0, 1, 4]])
+    with pytest.raises(AssertionError):
+        orc.neighbors(S)
