@@ -88,7 +88,8 @@ typedef struct dt_config {
   int profile;           /* 1: time the insertion kernels with CUDA events (dt_get_kernel_profile) */
   int neighbors;         /* 1: run the neighbourhood update inside dt_triangulate (otherwise it runs
                             on the first dt_get_neighbors call) */
-  int reserved[6];
+  int first_batch;       /* points per instance in the first insertion batch (BRIO); 0 = automatic (32) */
+  int reserved[5];
 } dt_config;
 
 typedef struct dt_stats {
@@ -148,7 +149,7 @@ typedef struct dt_kernel_profile {
   int64_t launches;
   double ms;             /* summed CUDA-event time on the context stream */
   double bytes;          /* algorithmic bytes (each record the kernel must touch, once) */
-  double flops;          /* FP64 operations of the predicate filters */
+  double flops;          /* floating-point operations of the first (FP32) predicate stage */
 } dt_kernel_profile;
 
 typedef struct dt_ctx dt_ctx;

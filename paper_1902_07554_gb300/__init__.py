@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
                 ("grid_cell", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("base_threshold", ctypes.c_int), ("validate", ctypes.c_int),
                 ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("first_batch", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class KernelProfile(ctypes.Structure):

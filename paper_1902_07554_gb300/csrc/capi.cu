@@ -37,7 +37,7 @@ static bool cfg_valid(const dt_config* c) {
   return c->divide >= 0 && c->divide <= 1 && c->primitive >= 0 && c->primitive <= 1 && c->weight >= 0 &&
          c->weight <= 3 && c->lp_rounds >= 0 && c->lp_rounds <= 1000 && c->epsilon >= 0 && c->epsilon <= 10 &&
          c->grid_cell > 0 && c->grid_cell <= 64 && c->base_threshold >= 0 && c->cavity_cap >= 0 &&
-         c->cavity_cap <= 4096;
+         c->cavity_cap <= 4096 && c->first_batch >= 0;
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {
@@ -90,6 +90,7 @@ extern "C" void dt_destroy(dt_ctx* c) {
   if (c->counters_host) cudaFreeHost(c->counters_host);
   for (int i = 0; i < 16; i++) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 16; i++) if (c->pev[i]) cudaEventDestroy(c->pev[i]);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

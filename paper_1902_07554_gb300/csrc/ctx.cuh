@@ -21,6 +21,7 @@ struct dt_ctx {
   int* counters_host = nullptr;          // pinned scratch for small read-backs (64 ints)
   cudaEvent_t ev[16];
   cudaEvent_t pev[16];                   // per-kernel profiling events
+  std::vector<cudaEvent_t> evpool;       // profile mode: events around every engine launch
   long long launches = 0;                // kernels launched by this context (all calls)
   // per-kernel profile of the last call (profile mode)
   struct KProf { const char* name; long long launches; double ms, bytes, flops; };

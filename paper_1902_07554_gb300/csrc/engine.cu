@@ -221,12 +221,38 @@ enum { CAND_OK = 0, CAND_LOST = 1, CAND_OVER = 2 };
 // stronger key -- every neighbour lies in the nominee's region or ring, and a
 // stronger key there belongs to a nominee whose region contains it, so the
 // weaker one would lose anyway.  Nominees go to a dense list.
+// Nominees go to NBUCKET lists by the top bits of their key, strongest
+// first: the cavity kernel takes them in that order, so the regions of strong
+// nominees are claimed early and weaker ones stop at their first contact.
+constexpr int NBUCKET = 8;
+__device__ __forceinline__ int key_bucket(unsigned long long key) {
+  return NBUCKET - 1 - (int)((uint32_t)key >> 29);
+}
+
+// Slot -> nominee: slots enumerate the buckets in order (bcnt: bucket sizes,
+// of which the first seg entries are stored; seg: the capacity of one list).
+// The caller keeps slot below the number stored, which k_nominate counts.
+__device__ __forceinline__ int nominee_at(const int* nom, const int* bcnt, int seg, int slot) {
+  int q = 0, base = 0;
+#pragma unroll
+  for (int b = 0; b < NBUCKET - 1; b++) {
+    const int c = min(bcnt[b], seg);
+    if (slot >= base + c) { base += c; q = b + 1; }
+    else break;
+  }
+  return nom[(int64_t)q * seg + (slot - base)];
+}
+
 template <int D>
-__global__ void k_nominate(TriView<D> T, const int* act, const int* nact_p, unsigned round, int* nom, int* nnom) {
+__global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, const int* nact_p, unsigned round,
+                                                  int* nom, int* nnom, int* bcnt, int seg) {
+  __shared__ int s_cnt[NBUCKET], s_base[NBUCKET];
+  if (threadIdx.x < NBUCKET) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int nact = *nact_p;
   bool take = false;
-  int p = -1;
+  int p = -1, bucket = -1;
   if (idx < nact) {
     p = act[idx];
     unsigned long long key = mkkey(round, p);
@@ -239,8 +265,33 @@ __global__ void k_nominate(TriView<D> T, const int* act, const int* nact_p, unsi
         if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) take = false;
       }
     }
+    if (take) bucket = key_bucket(key);
   }
-  warp_append(nom, nnom, take, p);
+  // offsets within the block per bucket (lanes grouped by bucket), then one
+  // global atomic per bucket and block
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(0xffffffffu, bucket);
+  const int leader = __ffs(grp) - 1;
+  int wbase = 0;
+  if (take && lane == leader) wbase = atomicAdd(&s_cnt[bucket], __popc(grp));
+  wbase = __shfl_sync(0xffffffffu, wbase, leader);
+  const int local = wbase + __popc(grp & ((1u << lane) - 1));
+  __syncthreads();
+  if (threadIdx.x < NBUCKET) {
+    const int cnt = s_cnt[threadIdx.x];
+    int gb = 0;
+    if (cnt) {
+      gb = atomicAdd(&bcnt[threadIdx.x], cnt);
+      const int stored = max(0, min(cnt, seg - gb));   // a full list drops the rest this round
+      if (stored) atomicAdd(nnom, stored);
+    }
+    s_base[threadIdx.x] = gb;
+  }
+  __syncthreads();
+  if (take) {
+    const int at = s_base[bucket] + local;
+    if (at < seg) nom[(int64_t)bucket * seg + at] = p;
+  }
 }
 
 // One warp per nominee grows its conflict region: each lane inspects one
@@ -250,16 +301,21 @@ __global__ void k_nominate(TriView<D> T, const int* act, const int* nact_p, unsi
 // the others become boundary facets (ring claim in claimA).
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
-                                                  CandScratch S) {
+                                                  CandScratch S, const int* bcnt) {
   const unsigned FULL = 0xffffffffu;
   int lane = threadIdx.x & 31;
   int nwarp = (gridDim.x * blockDim.x) >> 5;
   int nnom = min(*nnom_p, S.cap);
   constexpr int PER = 32 / (D + 1);
+  // the region list lives in shared memory while it fits (copied out at the end)
+  constexpr int SHC = 128;
+  __shared__ int s_region[4][SHC];
+  const bool in_shared = S.capC <= SHC && blockDim.x <= 128;
   for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < nnom; slot += nwarp) {
-    int p = nom[slot];
+    int p = nominee_at(nom, bcnt, S.cap, slot);
     unsigned long long key = mkkey(round, p);
-    int* C = S.cav + (int64_t)slot * S.capC;
+    int* Cg = S.cav + (int64_t)slot * S.capC;
+    int* C = in_shared ? s_region[threadIdx.x >> 5] : Cg;
     int* B = S.bnd + (int64_t)slot * S.capB;
     int t0 = T.loc[p];
     int status = CAND_OK;
@@ -286,12 +342,12 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
         if (!slot_ok(T, u)) {
           bad = true;
         } else {
+          const int4 vv = T.tv[u];                       // loaded beside the claim, not after it
           unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
           pbytes += 16;
           if (cC > key) {
             lost = true;                                 // inside a stronger region
           } else if (cC != key) {
-            int4 vv = T.tv[u];
             pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
             ptests++;
             if (!verts_ok(T, vv)) {
@@ -299,12 +355,14 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
             } else {
               int vt[4] = {vv.x, vv.y, vv.z, vv.w};
               if (in_conflict_x(T.pts, T.xs, T.gid, vt, p, D)) {
+                // both claims at once; the region claim decides, the ring claim
+                // can only raise claimA to a key that is no stronger than needed
                 unsigned long long o = atomicMax(&T.claimC[u], key);
-                if (o > key) {
+                unsigned long long o2 = atomicMax(&T.claimA[u], key);
+                if (o > key || o2 > key) {
                   lost = true;
                 } else if (o < key) {                    // first lane to claim it
-                  unsigned long long o2 = atomicMax(&T.claimA[u], key);
-                  if (o2 > key) lost = true; else addC = true;
+                  addC = true;
                   pbytes += 16 + 16 + 4;
                 }
               } else {
@@ -329,6 +387,8 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
       h = min(h + PER, nc0);                             // simplices appended now come next
       __syncwarp();
     }
+    if (in_shared && status == CAND_OK)
+      for (int q = lane; q < nc; q += 32) Cg[q] = C[q];
     if (T.prof) {
       for (int off = 16; off; off >>= 1) {
         pbytes += __shfl_down_sync(FULL, pbytes, off);
@@ -338,6 +398,10 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
     if (lane == 0) {
       if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
       S.meta[slot] = make_int4(nc, nbd, status, 0);
+      if (T.dbg) {   // [4] complete regions, [5] region simplices grown by all nominees
+        if (status == CAND_OK) atomicAdd(&T.dbg[4], 1ull);
+        atomicAdd(&T.dbg[5], (unsigned long long)nc);
+      }
       if (T.prof) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
     }
     __syncwarp();
@@ -435,12 +499,16 @@ __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, 
       T.tn[base + b] = nn;
     }
     __syncwarp();
-    // phase 3: retire the region; dead slots redirect to the first new simplex
+    // phase 3: retire the region.  A dead slot redirects to a new simplex
+    // that lies on one of its own boundary facets when it has one (the
+    // points it held are then a step or two away), else to the first one.
     for (int h = lane; h < nc; h += 32) {
       int t = C[h];
       *comp_ptr(T.tv, t, 0) = DEAD;
       *comp_ptr(T.tn, t, 0) = pack_nb(base, 0);
     }
+    __syncwarp();
+    for (int b = lane; b < nbd; b += 32) *comp_ptr(T.tn, nb_simplex(B[b]), 0) = pack_nb(base + b, 0);
     if (lane == 0) {
       T.state[p] = 1;
       T.loc[p] = base;
@@ -658,6 +726,17 @@ static double host_from_orderable(unsigned long long u) {
   double x;
   memcpy(&x, &b, 8);
   return x;
+}
+
+// Profile mode: events recorded between the engine's launches without any
+// synchronisation; the times are read once, after the last round.
+static cudaEvent_t prof_event(dt_ctx* c, size_t i) {
+  while (c->evpool.size() <= i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    c->evpool.push_back(e);
+  }
+  return c->evpool[i];
 }
 
 void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops) {
@@ -885,8 +964,9 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       for (int l = 0; l < 34; l++) lo32[l] = (int)loff[l];
       CUDA_OK(cudaMemcpyAsync(loffd, lo32.data(), 4 * 34, cudaMemcpyHostToDevice, s));
       k_scatter_levels<<<gpp, 256, (++c->launches, 0), s>>>(level, lrank, loffd, npts, llist);
-      // the first batch: about 64 points per instance (at least 4096 in all)
-      int64_t want = std::max<int64_t>(4096, 64 * (int64_t)ninst);
+      // the first batch: about first_batch points per instance
+      const int fb = c->cfg.first_batch > 0 ? c->cfg.first_batch : 32;
+      int64_t want = (int64_t)fb * ninst;
       first_level = 32;
       while (first_level > 0 && loff[33] - loff[first_level] < want) first_level--;
       if (getenv("GDT_NOBRIO")) first_level = 0;
@@ -905,7 +985,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       capC = c->cfg.cavity_cap;
       capB = D == 2 ? c->cfg.cavity_cap * 3 / 2 : c->cfg.cavity_cap * 2;
     }
-    int* nom = (int*)pool_get(c, "eng.nom", 4 * std::max<int64_t>(npts, 1));
+    int* nom = (int*)pool_get(c, "eng.nom", 4 * (size_t)NBUCKET * std::max<int64_t>(std::min<int64_t>(npts, int64_t(1) << 22), 1));
     int* walk = (int*)pool_get(c, "eng.walk", 4 * std::max<int64_t>(npts, 1));
     if (!nom || !walk) return set_err(c, DT_E_NOMEM, "nominee lists");
     // device counters: [0] active, [1] next active, [2] nominees, [3] winners, [4] walkers
@@ -917,6 +997,20 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     int last_sync_nact = nact;
     const bool prof = c->cfg.profile != 0;
     const int SYNC_EVERY = 4;
+    // profile records: (start event, end event, kernel)
+    struct ProfRec { int a, b, k; };
+    std::vector<ProfRec> recs;
+    size_t nev = 0;
+    auto mark = [&]() -> int {
+      if (!prof) return -1;
+      cudaEvent_t e = prof_event(c, nev);
+      if (!e) return -1;
+      cudaEventRecord(e, s);
+      return (int)nev++;
+    };
+    static const char* const knames[2][6] = {
+        {"k_nominate<2>", "k_cavity_w<2>", "k_insert_w<2>", "k_reloc_check<2>", "k_reloc_walk<2>", "k_activate<2>"},
+        {"k_nominate<3>", "k_cavity_w<3>", "k_insert_w<3>", "k_reloc_check<3>", "k_reloc_walk<3>", "k_activate<3>"}};
     if (nact > 0)
       k_pick<D><<<(unsigned)ceil_div(nact, 256), 256, (++c->launches, 0), s>>>(T, ain, nact, 1);
     while (nact > 0 || next_level >= 0) {
@@ -924,16 +1018,11 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       while (next_level >= 0 && nact <= last_batch / 4) {
         int m = (int)(loff[next_level + 1] - loff[next_level]);
         if (m > 0) {
-          if (prof) cudaEventRecord(c->pev[6], s);
+          const int a0 = mark();
           k_activate<D><<<(unsigned)ceil_div(m, 128), 128, (++c->launches, 0), s>>>(
               T, llist + loff[next_level], m, ain, cnt + 0, round + 1);
-          if (prof) {
-            cudaEventRecord(c->pev[7], s);
-            cudaEventSynchronize(c->pev[7]);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, c->pev[6], c->pev[7]);
-            prof_add(c, D == 2 ? "k_activate<2>" : "k_activate<3>", ms, 0, 0);
-          }
+          const int a1 = mark();
+          if (a0 >= 0 && a1 >= 0) recs.push_back({a0, a1, 5});
           nact += m;
           last_batch = nact;
           last_sync_nact = -1;         // activation changes the count: skip one progress check
@@ -956,28 +1045,34 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       S.count = cnt + 2;
       if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
       CUDA_OK(cudaMemsetAsync(cnt + 1, 0, 16, s));
+      CUDA_OK(cudaMemsetAsync(cnt + 8, 0, 4 * NBUCKET, s));
       unsigned gp = (unsigned)ceil_div(nact, 256);
       unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
-      if (prof) cudaEventRecord(c->pev[0], s);
-      k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2);
-      if (prof) cudaEventRecord(c->pev[1], s);
-      k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S);
-      if (prof) cudaEventRecord(c->pev[2], s);
+      int ev[6];
+      ev[0] = mark();
+      k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2, cnt + 8, capCand);
+      ev[1] = mark();
+      k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8);
+      ev[2] = mark();
       k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3);
-      if (prof) cudaEventRecord(c->pev[3], s);
+      ev[3] = mark();
       k_reloc_check<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, aout, cnt + 1, walk, cnt + 4, round + 1);
-      if (prof) cudaEventRecord(c->pev[4], s);
+      ev[4] = mark();
       k_reloc_walk<D><<<(unsigned)ceil_div(nact, 128), 128, (++c->launches, 0), s>>>(T, walk, cnt + 4, round + 1);
-      if (prof) cudaEventRecord(c->pev[5], s);
+      ev[5] = mark();
+      for (int q = 0; q < 5; q++)
+        if (ev[q] >= 0 && ev[q + 1] >= 0) recs.push_back({ev[q], ev[q + 1], q});
       if (getenv("GDT_DEBUG")) {
         int hc[5];
-        unsigned long long hd[4];
+        unsigned long long hd[6];
         cudaMemcpyAsync(hc, cnt, 20, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(hd, T.dbg, 32, cudaMemcpyDeviceToHost, s);
-        cudaMemsetAsync(T.dbg, 0, 32, s);
+        cudaMemcpyAsync(hd, T.dbg, 48, cudaMemcpyDeviceToHost, s);
+        cudaMemsetAsync(T.dbg, 0, 48, s);
         cudaStreamSynchronize(s);
-        fprintf(stderr, "round %u nact %d cand %d win %d walk %d steps %llu max %llu act_steps %llu act_max %llu\n",
-                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3]);
+        fprintf(stderr,
+                "round %u nact %d cand %d win %d walk %d steps %llu max %llu act_steps %llu act_max %llu "
+                "complete %llu grown %llu\n",
+                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3], hd[4], hd[5]);
       }
       k_move_count<<<1, 1, (++c->launches, 0), s>>>(cnt + 0, cnt + 1);
       std::swap(ain, aout);
@@ -985,17 +1080,6 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       if (check)
         k_check_mesh<D><<<(unsigned)ceil_div<int64_t>(total, 256), 256, (++c->launches, 0), s>>>(
             T, run.toff, run.tcount, ninst, round);
-      if (prof) {
-        CUDA_OK(cudaStreamSynchronize(s));
-        const char* names[5] = {D == 2 ? "k_nominate<2>" : "k_nominate<3>", D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>",
-                                D == 2 ? "k_insert_w<2>" : "k_insert_w<3>", D == 2 ? "k_reloc_check<2>" : "k_reloc_check<3>",
-                                D == 2 ? "k_reloc_walk<2>" : "k_reloc_walk<3>"};
-        for (int q = 0; q < 5; q++) {
-          float ms = 0;
-          cudaEventElapsedTime(&ms, c->pev[q], c->pev[q + 1]);
-          prof_add(c, names[q], ms, 0, 0);
-        }
-      }
       if (round % SYNC_EVERY != 0 && nact > 4096 && !check) continue;
       CUDA_OK(cudaMemcpyAsync(h, cnt + 0, 4, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -1022,12 +1106,20 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     }
     run.rounds = (int)round;
     if (failed) { grow *= 2; continue; }
+    if (prof && !recs.empty()) {
+      CUDA_OK(cudaStreamSynchronize(s));
+      for (const ProfRec& r : recs) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->evpool[r.a], c->evpool[r.b]);
+        prof_add(c, knames[D - 2][r.k], ms, 0, 0);
+      }
+    }
     if (profc) {
       unsigned long long hp[2];
       CUDA_OK(cudaMemcpyAsync(hp, profc, 16, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
-      // insphere filter: about 145 FP64 operations in 3D, 40 in 2D
-      prof_add(c, D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 40 : 145));
+      // FP32 insphere stage: about 220 operations in 3D (determinant and both permanents), 70 in 2D
+      prof_add(c, D == 2 ? "k_cavity_w<2>" : "k_cavity_w<3>", 0, (double)hp[0], (double)hp[1] * (D == 2 ? 70 : 220));
       unsigned long long hr[2] = {0, 0};
       CUDA_OK(cudaMemcpyAsync(hr, profc + 2, 16, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
