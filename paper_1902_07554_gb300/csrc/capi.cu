@@ -91,6 +91,7 @@ extern "C" void dt_destroy(dt_ctx* c) {
   for (int i = 0; i < 16; i++) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 16; i++) if (c->pev[i]) cudaEventDestroy(c->pev[i]);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

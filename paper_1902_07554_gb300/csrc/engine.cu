@@ -99,6 +99,24 @@ __device__ __forceinline__ int orient_tuple(const TriView<D>& T, const int4& v) 
 // One thread per instance: the first D+1 affinely independent points (in
 // index order) form a positively oriented simplex, surrounded by D+1 ghost
 // simplices (infinite vertex + one hull facet each).
+// Round state of the device-driven insertion loop (a CUDA graph whose
+// conditional WHILE node repeats one round: begin, activate, nominate,
+// cavity, insert, relocate, end).  The kernels take their round, active lists
+// and activation range from here when the pointer is non-null, and from their
+// parameters when the host drives the rounds (profile and debug runs).
+struct EngCtl {
+  unsigned round;      // current round
+  int* ain;            // active points of this round
+  int* aout;           // active points of the next round
+  int next_level;      // next activation level (-1: none left)
+  int last_batch;      // active count right after the last activation
+  int act_lo, act_n;   // this round's activation range in the level list
+  int last_nact;       // active count after the previous round
+  int stalled;         // consecutive rounds without an insertion
+  int activated;       // points activated this round
+  int done;            // 0 running; 1 finished; 2 device error; 3 stalled; 4 round limit
+};
+
 template <int D>
 __global__ void k_init(TriView<D> T, int ninst, const long long* poff, const int* toff, int* inst_status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,12 +263,15 @@ __device__ __forceinline__ int nominee_at(const int* nom, const int* bcnt, int s
 
 template <int D>
 __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, const int* nact_p, unsigned round,
-                                                  int* nom, int* nnom, int* bcnt, int seg) {
+                                                  int* nom, int* nnom, int* bcnt, int seg, const EngCtl* ctl) {
   __shared__ int s_cnt[NBUCKET], s_base[NBUCKET];
+  if (ctl) { act = ctl->ain; round = ctl->round; }
+  const int nact = *nact_p;
+  for (int64_t blk = (int64_t)blockIdx.x * blockDim.x; blk < nact; blk += (int64_t)gridDim.x * blockDim.x) {
+  __syncthreads();
   if (threadIdx.x < NBUCKET) s_cnt[threadIdx.x] = 0;
   __syncthreads();
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int nact = *nact_p;
+  const int64_t idx = blk + threadIdx.x;
   bool take = false;
   int p = -1, bucket = -1;
   if (idx < nact) {
@@ -292,6 +313,7 @@ __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, 
     const int at = s_base[bucket] + local;
     if (at < seg) nom[(int64_t)bucket * seg + at] = p;
   }
+  }
 }
 
 // One warp per nominee grows its conflict region: each lane inspects one
@@ -301,8 +323,9 @@ __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, 
 // the others become boundary facets (ring claim in claimA).
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
-                                                  CandScratch S, const int* bcnt) {
+                                                  CandScratch S, const int* bcnt, const EngCtl* ctl) {
   const unsigned FULL = 0xffffffffu;
+  if (ctl) round = ctl->round;
   int lane = threadIdx.x & 31;
   int nwarp = (gridDim.x * blockDim.x) >> 5;
   int nnom = min(*nnom_p, S.cap);
@@ -413,8 +436,9 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
 // Winners replace their region by the star of new simplices in fresh slots.
 template <int D>
 __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, CandScratch S, const int* nnom_p,
-                                                  int* nwin) {
+                                                  int* nwin, const EngCtl* ctl) {
   const unsigned FULL = 0xffffffffu;
+  if (ctl) round = ctl->round;
   int lane = threadIdx.x & 31;
   int nwarp = (gridDim.x * blockDim.x) >> 5;
   int total = min(*nnom_p, S.cap);
@@ -564,27 +588,32 @@ __device__ int walk_to(const TriView<D>& T, int s, int p, int limit, int* steps_
 // to the walker list, the others make the next round's pick right away.
 template <int D>
 __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, int* act_out, int* nact_out,
-                              int* walk, int* nwalk, unsigned next_round) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int nact = *nact_p;
-  bool keep = false, walker = false;
-  int p = -1;
-  if (idx < nact) {
-    p = act[idx];
-    if (T.state[p] == 0) {
-      keep = true;
-      int s = T.loc[p];
-      if (*comp_ptr(T.tv, s, 0) == DEAD) walker = true;
-      else atomicMax(&T.claimC[s], mkkey(next_round, p));
+                              int* walk, int* nwalk, unsigned next_round, const EngCtl* ctl) {
+  if (ctl) { act = ctl->ain; act_out = ctl->aout; next_round = ctl->round + 1; }
+  const int nact = *nact_p;
+  // warp-uniform grid-stride loop (warp_append needs every lane)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nact;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = base + (threadIdx.x & 31);
+    bool keep = false, walker = false;
+    int p = -1;
+    if (idx < nact) {
+      p = act[idx];
+      if (T.state[p] == 0) {
+        keep = true;
+        int s = T.loc[p];
+        if (*comp_ptr(T.tv, s, 0) == DEAD) walker = true;
+        else atomicMax(&T.claimC[s], mkkey(next_round, p));
+      }
     }
-  }
-  warp_append(act_out, nact_out, keep, p);
-  warp_append(walk, nwalk, walker, p);
-  if (T.prof && idx < nact) {
-    // act 4, state 1, loc 4, slot word 4, pick 8, output 4
-    unsigned long long b = 25;
-    for (int off = 16; off; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[3], b);
+    warp_append(act_out, nact_out, keep, p);
+    warp_append(walk, nwalk, walker, p);
+    if (T.prof) {
+      // act 4, state 1, loc 4, slot word 4, pick 8, output 4
+      unsigned long long b = idx < nact ? 25 : 0;
+      for (int off = 16; off; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[3], b);
+    }
   }
 }
 
@@ -593,31 +622,36 @@ __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, i
 // conflict with the point, make its pick for the next round, and append it
 // to the active list.
 template <int D>
-__global__ void __launch_bounds__(128, 8) k_activate(TriView<D> T, const int* list, int m, int* act, int* nact, unsigned next_round) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  bool ok = false;
-  int p = -1;
-  if (idx < m) {
-    p = list[idx];
-    int s = T.loc[p];
-    if (T.hint) {
-      int h = T.hint[hint_cell(T, p)];
-      if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
+__global__ void __launch_bounds__(128, 8) k_activate(TriView<D> T, const int* list, int m, int* act, int* nact,
+                                                  unsigned next_round, const EngCtl* ctl) {
+  if (ctl) { list += ctl->act_lo; m = ctl->act_n; act = ctl->ain; next_round = ctl->round; }
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < m;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = base + (threadIdx.x & 31);
+    bool ok = false;
+    int p = -1;
+    if (idx < m) {
+      p = list[idx];
+      int s = T.loc[p];
+      if (T.hint) {
+        int h = T.hint[hint_cell(T, p)];
+        if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
+      }
+      for (int hop = 0; hop < (1 << 20) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
+        s = nb_simplex(*comp_ptr(T.tn, s, 0));
+      int steps = 0;
+      int r = walk_to(T, s, p, 1 << 22, &steps);
+      if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
+      if (r < 0) {
+        set_error(T.st, DT_E_TIMEOUT, 4);
+      } else {
+        T.loc[p] = r;
+        atomicMax(&T.claimC[r], mkkey(next_round, p));
+        ok = true;
+      }
     }
-    for (int hop = 0; hop < (1 << 20) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
-      s = nb_simplex(*comp_ptr(T.tn, s, 0));
-    int steps = 0;
-    int r = walk_to(T, s, p, 1 << 22, &steps);
-    if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
-    if (r < 0) {
-      set_error(T.st, DT_E_TIMEOUT, 4);
-    } else {
-      T.loc[p] = r;
-      atomicMax(&T.claimC[r], mkkey(next_round, p));
-      ok = true;
-    }
+    warp_append(act, nact, ok, p);
   }
-  warp_append(act, nact, ok, p);
 }
 
 // Opt-in self-check of the mesh (GDT_CHECK): every live simplex's links are
@@ -657,19 +691,23 @@ __global__ void k_check_mesh(TriView<D> T, const int* toff, const int* tcount, i
 }
 
 template <int D>
-__global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p, unsigned next_round) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= *nwalk_p) return;
-  int p = walk[idx];
-  int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
-  int steps = 0;
-  int r = walk_to(T, s, p, 1 << 22, &steps);
-  if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); return; }
-  T.loc[p] = r;
-  atomicMax(&T.claimC[r], mkkey(next_round, p));
-  // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
-  if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
-  if (T.dbg) { atomicAdd(&T.dbg[0], (unsigned long long)steps); atomicMax(&T.dbg[1], (unsigned long long)steps); }
+__global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p,
+                                                    unsigned next_round, const EngCtl* ctl) {
+  if (ctl) next_round = ctl->round + 1;
+  const int nwalk = *nwalk_p;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nwalk;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int p = walk[idx];
+    int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
+    int steps = 0;
+    int r = walk_to(T, s, p, 1 << 22, &steps);
+    if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); continue; }
+    T.loc[p] = r;
+    atomicMax(&T.claimC[r], mkkey(next_round, p));
+    // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
+    if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
+    if (T.dbg) { atomicAdd(&T.dbg[0], (unsigned long long)steps); atomicMax(&T.dbg[1], (unsigned long long)steps); }
+  }
 }
 
 __device__ __forceinline__ unsigned long long ord_key(double x) {
@@ -712,6 +750,58 @@ __global__ void k_scatter_levels(const int* level, const int* rank, const int* l
 __global__ void k_move_count(int* dst, int* src) {
   *dst = *src;
   *src = 0;
+}
+
+// Start of a device-driven round: activate the next level(s) when the active
+// set has drained to a quarter of the last batch (the rule of the host
+// loop), advance the round, clear the round's counters.  One thread.
+__global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  EngCtl& C = *ctl;
+  int nact = cnt[0];
+  int lo = -1, hi = -1;
+  while (C.next_level >= 0 && nact <= C.last_batch / 4) {
+    const int l = C.next_level;
+    const int m = loffd[l + 1] - loffd[l];
+    if (m > 0) {
+      if (hi < 0) hi = loffd[l + 1];
+      lo = loffd[l];
+      nact += m;
+      C.last_batch = nact;
+    }
+    C.next_level--;
+  }
+  C.act_lo = lo < 0 ? 0 : lo;
+  C.act_n = lo < 0 ? 0 : hi - lo;
+  C.activated = C.act_n;
+  if (nact > 0) C.round++;
+  if (C.round > 400000) C.done = 4;
+  cnt[1] = cnt[2] = cnt[3] = cnt[4] = 0;
+  for (int b = 0; b < NBUCKET; b++) cnt[8 + b] = 0;
+}
+
+// End of a device-driven round: the next active list becomes current; the
+// loop ends when nothing is left, on a device error, after 4 rounds in a row
+// without an insertion (a cavity overflowed its scratch: the host grows it),
+// or at the round limit.
+__global__ void k_round_end(EngCtl* ctl, int* cnt, const DevStatus* st, cudaGraphConditionalHandle handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  EngCtl& C = *ctl;
+  const int had = cnt[0];
+  const int nnew = cnt[1];
+  cnt[0] = nnew;
+  cnt[1] = 0;
+  int* t = C.ain;
+  C.ain = C.aout;
+  C.aout = t;
+  if (C.done == 0) {
+    if (st->error) C.done = 2;
+    else if (nnew == 0 && C.next_level < 0) C.done = 1;
+    else if (had > 0 && cnt[3] == 0 && ++C.stalled >= 4) C.done = 3;
+    else if (cnt[3] > 0) C.stalled = 0;
+  }
+  C.last_nact = nnew;
+  cudaGraphSetConditional(handle, C.done == 0 ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- host
@@ -805,6 +895,118 @@ int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t n
   else k_make_x32<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)pts, pinst, npts, xo, xs);
   CUDA_OK(cudaStreamSynchronize(s));   // hxo goes out of scope
   return 0;
+}
+
+// Capture stream of the context (created on first use).
+static cudaStream_t capture_stream(dt_ctx* c) {
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+  }
+  return c->cap_stream;
+}
+
+// Every insertion round on the device: a graph whose conditional WHILE node
+// repeats begin / activate / nominate / cavity / insert / relocate / end
+// until k_round_end clears the condition.  Grids are fixed (the kernels loop
+// over their items); the candidate scratch is sized for the largest round.
+// A round loop that stalls on cavity-scratch overflow is relaunched with
+// twice the scratch; the state lives on the device, so it resumes.
+template <int D>
+static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, int* cnt, const int* loffd,
+                        const std::vector<int64_t>& loff, const int* llist, int* nom, int* walk, int* act0, int* act1,
+                        int nact, int last_batch, int next_level, int capC, int capB, unsigned* round_out,
+                        bool* failed) {
+  cudaStream_t s = c->stream;
+  cudaStream_t cs = capture_stream(c);
+  EngCtl* ctl = (EngCtl*)pool_get(c, "eng.ctl", sizeof(EngCtl));
+  if (!cs || !ctl) return set_err(c, DT_E_NOMEM, "round graph");
+  EngCtl h0;
+  memset(&h0, 0, sizeof(h0));
+  h0.ain = act0;
+  h0.aout = act1;
+  h0.next_level = next_level;
+  h0.last_batch = last_batch;
+  h0.last_nact = nact;
+  CUDA_OK(cudaMemcpyAsync(ctl, &h0, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
+  const int capCand = (int)std::max<int64_t>(1, std::min<int64_t>(npts, int64_t(1) << 22));
+  int64_t max_level = 1;
+  for (size_t l = 0; l + 1 < loff.size(); l++) max_level = std::max<int64_t>(max_level, loff[l + 1] - loff[l]);
+  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div<int64_t>(npts, 256), 152 * 8);
+  const unsigned gr = (unsigned)std::min<int64_t>(ceil_div<int64_t>(npts, 128), 152 * 16);
+  const unsigned ga = (unsigned)std::min<int64_t>(ceil_div<int64_t>(max_level, 128), 152 * 16);
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
+  EngCtl h1;
+  memset(&h1, 0, sizeof(h1));
+  for (int grow = 0;; grow++) {
+    CandScratch S;
+    S.cap = capCand;
+    S.capC = capC << grow;
+    S.capB = capB << grow;
+    S.cand = (int*)pool_get(c, "eng.cand", 4 * (size_t)capCand);
+    S.meta = (int4*)pool_get(c, "eng.meta", 16 * (size_t)capCand);
+    S.cav = (int*)pool_get(c, "eng.cav", 4 * (size_t)capCand * S.capC);
+    S.bnd = (int*)pool_get(c, "eng.bnd", 4 * (size_t)capCand * S.capB);
+    S.outer = (int*)pool_get(c, "eng.outer", 4 * (size_t)capCand * S.capB);
+    S.count = cnt + 2;
+    if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    cudaGraphConditionalHandle hc = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      k_round_begin<<<1, 32, 0, cs>>>(ctl, cnt, loffd);
+      k_activate<D><<<ga, 128, 0, cs>>>(T, llist, 0, nullptr, cnt + 0, 0, ctl);
+      k_nominate<D><<<gn, 256, 0, cs>>>(T, nullptr, cnt + 0, 0, nom, cnt + 2, cnt + 8, capCand, ctl);
+      k_cavity_w<D><<<gw, 128, 0, cs>>>(T, nom, cnt + 2, 0, S, cnt + 8, ctl);
+      k_insert_w<D><<<gw, 128, 0, cs>>>(T, 0, S, cnt + 2, cnt + 3, ctl);
+      k_reloc_check<D><<<gn, 256, 0, cs>>>(T, nullptr, cnt + 0, nullptr, cnt + 1, walk, cnt + 4, 0, ctl);
+      k_reloc_walk<D><<<gr, 128, 0, cs>>>(T, walk, cnt + 4, 0, ctl);
+      k_round_end<<<1, 32, 0, cs>>>(ctl, cnt, c->status, hc);
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(cs, &captured);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gx, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (gx) cudaGraphExecDestroy(gx);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(c, gdt_cuda_fail(e, "round graph", __FILE__, __LINE__), "round graph");
+    const unsigned r0 = h1.round;
+    CUDA_OK(cudaMemcpyAsync(&h1, ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    c->launches += 1 + 8 * (int64_t)(h1.round - r0 + 1);
+    if (h1.done == 3 && c->status_host->overflow_cav && grow < 8) {
+      // cavities outgrew their scratch: twice the room, same state
+      CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));
+      EngCtl h2 = h1;
+      h2.done = 0;
+      h2.stalled = 0;
+      CUDA_OK(cudaMemcpyAsync(ctl, &h2, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      continue;
+    }
+    break;
+  }
+  *round_out = h1.round;
+  if (h1.done == 1) return 0;
+  if (h1.done == 2) {
+    if (c->status_host->error == DT_E_OVERFLOW && c->status_host->detail == 1) { *failed = true; return 0; }
+    return check_status(c, "insertion round");
+  }
+  if (h1.done == 4) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
+  return set_err(c, DT_E_INTERNAL, "insertion rounds made no progress");
 }
 
 template <int D>
@@ -1011,8 +1213,18 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     static const char* const knames[2][6] = {
         {"k_nominate<2>", "k_cavity_w<2>", "k_insert_w<2>", "k_reloc_check<2>", "k_reloc_walk<2>", "k_activate<2>"},
         {"k_nominate<3>", "k_cavity_w<3>", "k_insert_w<3>", "k_reloc_check<3>", "k_reloc_walk<3>", "k_activate<3>"}};
+    // Profile and debug runs drive the rounds from the host (events and
+    // checks between launches); otherwise one CUDA graph runs every round.
+    const bool host_loop = prof || getenv("GDT_DEBUG") || getenv("GDT_CHECK");
     if (nact > 0)
       k_pick<D><<<(unsigned)ceil_div(nact, 256), 256, (++c->launches, 0), s>>>(T, ain, nact, 1);
+    if (!host_loop && (nact > 0 || next_level >= 0)) {
+      int rc = graph_rounds<D>(c, T, run, npts, cnt, loffd, loff, llist, nom, walk, act0, act1, nact, last_batch,
+                               next_level, capC, capB, &round, &failed);
+      if (rc) return rc;
+      nact = 0;
+      next_level = -1;
+    }
     while (nact > 0 || next_level >= 0) {
       // activate the next batch when the active set has drained to a quarter
       while (next_level >= 0 && nact <= last_batch / 4) {
@@ -1020,7 +1232,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
         if (m > 0) {
           const int a0 = mark();
           k_activate<D><<<(unsigned)ceil_div(m, 128), 128, (++c->launches, 0), s>>>(
-              T, llist + loff[next_level], m, ain, cnt + 0, round + 1);
+              T, llist + loff[next_level], m, ain, cnt + 0, round + 1, nullptr);
           const int a1 = mark();
           if (a0 >= 0 && a1 >= 0) recs.push_back({a0, a1, 5});
           nact += m;
@@ -1050,15 +1262,18 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
       int ev[6];
       ev[0] = mark();
-      k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2, cnt + 8, capCand);
+      k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2, cnt + 8, capCand,
+                                                        nullptr);
       ev[1] = mark();
-      k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8);
+      k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8, nullptr);
       ev[2] = mark();
-      k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3);
+      k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3, nullptr);
       ev[3] = mark();
-      k_reloc_check<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, aout, cnt + 1, walk, cnt + 4, round + 1);
+      k_reloc_check<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, aout, cnt + 1, walk, cnt + 4, round + 1,
+                                                           nullptr);
       ev[4] = mark();
-      k_reloc_walk<D><<<(unsigned)ceil_div(nact, 128), 128, (++c->launches, 0), s>>>(T, walk, cnt + 4, round + 1);
+      k_reloc_walk<D><<<(unsigned)ceil_div(nact, 128), 128, (++c->launches, 0), s>>>(T, walk, cnt + 4, round + 1,
+                                                                                      nullptr);
       ev[5] = mark();
       for (int q = 0; q < 5; q++)
         if (ev[q] >= 0 && ev[q + 1] >= 0) recs.push_back({ev[q], ev[q + 1], q});
