@@ -302,6 +302,9 @@ def main():
     ap.add_argument("--workload", default="uniform3d_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--divide", default="sample", choices=["sample", "kd"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-rounds", action="store_true",
+                    help="drive every insertion round from the host (profile mode) in all steps, so that a "
+                         "kernel profiler lists each launch; the timed value then includes the event overhead")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -325,8 +328,8 @@ def main():
     stream = torch.cuda.Stream(device=local)       # one explicit stream for torch and the library
     torch.cuda.set_stream(stream)
     # neighbors=1: the merge's neighbourhood update runs inside every step
-    tri = Triangulator(local, stream=stream.cuda_stream, divide=0 if args.divide == "sample" else 1, profile=0,
-                       neighbors=1)
+    tri = Triangulator(local, stream=stream.cuda_stream, divide=0 if args.divide == "sample" else 1,
+                       profile=1 if args.host_rounds else 0, neighbors=1)
     P = gen_points(w, seed_offset=rank)
     n = w["n"]
     P_dev = torch.from_numpy(P).to(f"cuda:{local}")
@@ -384,7 +387,7 @@ def main():
             a = prof_tot.setdefault(kp["name"], dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
             for key in ("ms", "launches", "bytes", "flops"):
                 a[key] += kp[key]
-    tri.configure(profile=0)
+    tri.configure(profile=1 if args.host_rounds else 0)
 
     # ---------------- end to end: pinned host buffers through the C ABI
     P_pin = torch.from_numpy(P).pin_memory()
@@ -438,6 +441,7 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "dim": w["dim"], "k": w["k"], "sample_frac": w["frac"],
                    "divide": args.divide, "primitive": "grid", "weight": "log", "neighbors": True,
+                   "rounds": "host-driven (profile mode)" if args.host_rounds else "one CUDA graph per engine run",
                    "l2": "flushed before every step (256 MiB write); working set > L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,

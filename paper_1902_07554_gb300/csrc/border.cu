@@ -16,6 +16,7 @@
 // contributes all its points to vertices(B).
 #include <cmath>
 
+#include "bbox.cuh"
 #include "border.cuh"
 #include "pipeline.cuh"
 
@@ -32,17 +33,15 @@ __device__ __forceinline__ double from_orderable_key(unsigned long long u) {
   unsigned long long b = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
   return __longlong_as_double((long long)b);
 }
-__global__ void k_init_ubox(unsigned long long* ubox, int k) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 6 * k) ubox[i] = (i % 6) < 3 ? ~0ull : 0ull;
-}
 
 struct GridView {
   double lo[3], h[MAXLEV];       // origin, cell edge per level
+  double inv_h0;                 // 1 / h[0]
   int dims[MAXLEV][3];
   long long off[MAXLEV];         // start of each level's masks
   int levels;
   const unsigned long long* mask;
+  const unsigned long long* dil; // per cell: OR of the masks of its 3^d block (same layout)
 };
 
 template <int D>
@@ -87,6 +86,27 @@ __global__ void k_pyramid(GridView G, int lev, unsigned long long* mask) {
   mask[G.off[lev] + id] = m;
 }
 
+// OR of the masks of the 3^d block of cells around each cell of one level.
+template <int D>
+__global__ void k_dilate_mask(GridView G, int lev, const unsigned long long* mask, unsigned long long* dil) {
+  long long ncell = (long long)G.dims[lev][0] * G.dims[lev][1] * (D == 3 ? G.dims[lev][2] : 1);
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= ncell) return;
+  int x[3] = {0, 0, 0};
+  long long r = id;
+  for (int c = 0; c < D; c++) { x[c] = (int)(r % G.dims[lev][c]); r /= G.dims[lev][c]; }
+  unsigned long long m = 0;
+  for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++)
+    for (int dy = -1; dy <= 1; dy++)
+      for (int dx = -1; dx <= 1; dx++) {
+        int y[3] = {x[0] + dx, x[1] + dy, x[2] + dz};
+        bool ok = true;
+        for (int c = 0; c < D; c++) ok &= y[c] >= 0 && y[c] < G.dims[lev][c];
+        if (ok) m |= mask[cell_index<D>(G, lev, y)];
+      }
+  dil[G.off[lev] + id] = m;
+}
+
 // ---------------------------------------------------------------- shapes
 // A closed ball (center, radius) or a closed halfspace {x : n.(x - a) >= -slack}.
 struct Shape {
@@ -119,70 +139,121 @@ __device__ __forceinline__ bool box_hits(const Shape& S, const double* blo, cons
 }
 
 // Is there a cell, occupied by a partition in `others`, that the shape meets?
+// Balls are handled in grid units (u = (x - lo) / h0) and FP32, with a
+// margin of 2^-8 cell + 2^-20 |u| on the radius that covers the rounding of
+// u and of the box tests many times over.  The
+// cell of level l holding u is floor(u / 2^l), an exact scaling.  First, at
+// the finest level whose cell edge is at least the radius, the ball lies in
+// the 3^d block around its centre's cell: one load of that block's OR-ed
+// mask settles most simplices.  Otherwise a depth-first search descends the
+// pyramid (one frame per level).  Halfspaces (ghost simplices) are tested in
+// world coordinates; their search answers "hit" after 64 cells (a
+// conservative answer: the border may only grow).
+template <int D>
+__device__ __forceinline__ bool unit_box_hits(const float* u, float ru2, const int* x, float w) {
+  float d2 = 0;
+  for (int c = 0; c < D; c++) {
+    const float lo = x[c] * w, hi = lo + w;
+    const float v = u[c] < lo ? lo - u[c] : (u[c] > hi ? u[c] - hi : 0.0f);
+    d2 = fmaf(v, v, d2);
+  }
+  return d2 <= ru2;
+}
+
+// 2^-l as a float, exactly (no division).
+__device__ __forceinline__ float pow2f_neg(int l) { return __int_as_float((127 - l) << 23); }
+
 template <int D>
 __device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long others) {
-  // start level: the finest level where the shape's bounding range spans at most 3 cells
   int lev = G.levels - 1;
-  int lo_[3], hi_[3];
+  int lo_[3] = {0, 0, 0}, hi_[3] = {0, 0, 0};
+  float u[3] = {0, 0, 0}, ru = 0, ru2 = 0;
   if (!S.half) {
+    float umax = 0;
+    for (int c = 0; c < D; c++) {
+      u[c] = (float)((S.c[c] - G.lo[c]) * G.inv_h0);
+      umax = fmaxf(umax, fabsf(u[c]));
+    }
+    if (!(umax < 3e7f)) return true;
+    // margin: 2^-8 cell, plus 2^-20 |u| for the FP32 rounding of u and of the box tests
+    ru = (float)(S.r * G.inv_h0) * 1.0001f + 0.00390625f + umax * 9.5367431640625e-07f;
+    ru2 = ru * ru * 1.0001f;
+    if (!(ru2 < 1e12f)) return true;
     for (int l = 0; l < G.levels; l++) {
-      bool small = true;
+      if (ru > (float)(1 << l)) continue;
+      int x[3] = {0, 0, 0};
+      bool inside = true;
       for (int c = 0; c < D; c++) {
-        double a = floor((S.c[c] - S.r - G.lo[c]) / G.h[l]);
-        double b = floor((S.c[c] + S.r - G.lo[c]) / G.h[l]);
-        small &= (b - a) <= 2.0;
+        const float f = floorf(u[c] * pow2f_neg(l));
+        inside &= f >= 0 && f < G.dims[l][c];
+        x[c] = inside ? (int)f : 0;
       }
+      if (inside && !(G.dil[cell_index<D>(G, l, x)] & others)) return false;
+      break;
+    }
+    // the finest level where the ball's range spans at most 3 cells per axis
+    for (int l = 0; l < G.levels; l++) {
+      const float sc = pow2f_neg(l);
+      bool small = true;
+      for (int c = 0; c < D; c++) small &= floorf((u[c] + ru) * sc) - floorf((u[c] - ru) * sc) <= 2.0f;
       if (small) { lev = l; break; }
     }
+    const float sc = pow2f_neg(lev);
     for (int c = 0; c < D; c++) {
-      double fa = floor((S.c[c] - S.r - G.lo[c]) / G.h[lev]);
-      double fb = floor((S.c[c] + S.r - G.lo[c]) / G.h[lev]);
-      lo_[c] = (int)fmax(0.0, fmin(fa, (double)G.dims[lev][c] - 1));
-      hi_[c] = (int)fmax(0.0, fmin(fb, (double)G.dims[lev][c] - 1));
+      const float fa = floorf((u[c] - ru) * sc), fb = floorf((u[c] + ru) * sc);
       if (fb < 0 || fa > G.dims[lev][c] - 1) return false;   // ball outside the grid
+      lo_[c] = (int)fmaxf(0.0f, fa);
+      hi_[c] = (int)fminf(fb, (float)(G.dims[lev][c] - 1));
     }
   } else {
     for (int c = 0; c < D; c++) { lo_[c] = 0; hi_[c] = G.dims[lev][c] - 1; }
   }
-  // depth-first search; stack entries (level, cell coords)
-  int stk[192][4];
-  int sp = 0;
+  struct Frame { int x[3]; int child; };
+  Frame st[MAXLEV + 1];
+  int visits = 0;
   for (int z = (D == 3 ? lo_[2] : 0); z <= (D == 3 ? hi_[2] : 0); z++)
     for (int y = lo_[1]; y <= hi_[1]; y++)
       for (int x = lo_[0]; x <= hi_[0]; x++) {
-        if (sp >= 192) return true;   // stack exhausted: conservative answer
-        stk[sp][0] = lev; stk[sp][1] = x; stk[sp][2] = y; stk[sp][3] = z;
-        sp++;
+        int depth = 0;
+        st[0].x[0] = x; st[0].x[1] = y; st[0].x[2] = z; st[0].child = -1;
+        while (depth >= 0) {
+          Frame& f = st[depth];
+          const int l = lev - depth;
+          if (f.child < 0) {
+            const unsigned long long m = G.mask[cell_index<D>(G, l, f.x)];
+            bool hit = (m & others) != 0;
+            if (hit) {
+              if (!S.half) {
+                hit = unit_box_hits<D>(u, ru2, f.x, (float)(1 << l));
+              } else {
+                if (++visits > 64) return true;
+                double blo[3], bhi[3];
+                for (int c = 0; c < D; c++) {
+                  blo[c] = G.lo[c] + f.x[c] * G.h[l];
+                  bhi[c] = G.lo[c] + (f.x[c] + 1) * G.h[l];
+                  const double e = 1e-12 * (fabs(blo[c]) + fabs(bhi[c]) + G.h[l]);
+                  blo[c] -= e; bhi[c] += e;
+                }
+                hit = box_hits<D>(S, blo, bhi);
+              }
+            }
+            if (!hit) { depth--; continue; }
+            if (l == 0) return true;
+            f.child = 0;
+          }
+          if (f.child >= (1 << D)) { depth--; continue; }
+          const int k = f.child++;
+          Frame& nf = st[depth + 1];
+          bool ok = true;
+          for (int c = 0; c < 3; c++) {
+            nf.x[c] = c < D ? 2 * f.x[c] + ((k >> c) & 1) : 0;
+            if (c < D) ok &= nf.x[c] < G.dims[l - 1][c];
+          }
+          if (!ok) continue;
+          nf.child = -1;
+          depth++;
+        }
       }
-  while (sp > 0) {
-    sp--;
-    int l = stk[sp][0];
-    int x[3] = {stk[sp][1], stk[sp][2], stk[sp][3]};
-    unsigned long long m = G.mask[cell_index<D>(G, l, x)];
-    if (!(m & others)) continue;
-    double blo[3], bhi[3];
-    for (int c = 0; c < D; c++) {
-      blo[c] = G.lo[c] + x[c] * G.h[l];
-      bhi[c] = G.lo[c] + (x[c] + 1) * G.h[l];
-      // slack for the rounding of the box corners
-      double e = 1e-12 * (fabs(blo[c]) + fabs(bhi[c]) + G.h[l]);
-      blo[c] -= e; bhi[c] += e;
-    }
-    if (!box_hits<D>(S, blo, bhi)) continue;
-    if (l == 0) return true;
-    for (int k = 0; k < (1 << D); k++) {
-      int y[3] = {0, 0, 0};
-      bool ok = true;
-      for (int c = 0; c < D; c++) {
-        y[c] = 2 * x[c] + ((k >> c) & 1);
-        ok &= y[c] < G.dims[l - 1][c];
-      }
-      if (!ok) continue;
-      if (sp >= 192) return true;
-      stk[sp][0] = l - 1; stk[sp][1] = y[0]; stk[sp][2] = y[1]; stk[sp][3] = y[2];
-      sp++;
-    }
-  }
   return false;
 }
 
@@ -276,6 +347,92 @@ __device__ bool circumball(const typename PT<D>::T* P, const int4& v, Shape& S) 
   return true;
 }
 
+// The same ball from the FP32 copies of the points (X = fl32(x - o), X.w = eta;
+// see predicates.cuh): every FP32 difference d is within e(d) = eta + u32 |d|
+// / (1 - u32) of the exact one, so with D = |d| + e(d) the determinant and the
+// numerators N_j are off by at most P(D) - P(|d|) + 1e-5 P(D) (P: their
+// permanents).  The centre offset N / (2 det) then follows as in the FP64 ball,
+// the vertex a itself is off by at most eta / 2 per coordinate, and the
+// radius covers both, plus a relative 1e-8 so that the ball also contains the
+// FP64 ball (the FP32 ball is only used to rule a simplex out).  Returns false
+// when the bound cannot be established.
+template <int D>
+__device__ bool circumball_f32(const float4* X, const double* o, const int4& v, Shape& S) {
+  const float4 a = X[v.x];
+  const float eta = a.w;
+  float N[3] = {0, 0, 0}, EN[3] = {0, 0, 0}, det, Edet, pdd;
+  if (D == 2) {
+    const float4 b = X[v.y], c = X[v.z];
+    const float bx = b.x - a.x, by = b.y - a.y, cx_ = c.x - a.x, cy_ = c.y - a.y;
+    const float Bx = f32_up(bx, eta), By = f32_up(by, eta), Cx = f32_up(cx_, eta), Cy = f32_up(cy_, eta);
+    const float lb = bx * bx + by * by, lc = cx_ * cx_ + cy_ * cy_;
+    const float LB = Bx * Bx + By * By, LC = Cx * Cx + Cy * Cy;
+    det = bx * cy_ - by * cx_;
+    const float p0d = fabsf(bx * cy_) + fabsf(by * cx_);
+    pdd = Bx * Cy + By * Cx;
+    Edet = (pdd - p0d) + 1e-5f * pdd;
+    N[0] = lb * cy_ - lc * by;
+    N[1] = lc * bx - lb * cx_;
+    const float p00 = lb * fabsf(cy_) + lc * fabsf(by), p01 = lc * fabsf(bx) + lb * fabsf(cx_);
+    const float pd0 = LB * Cy + LC * By, pd1 = LC * Bx + LB * Cx;
+    EN[0] = (pd0 - p00) + 1e-5f * pd0;
+    EN[1] = (pd1 - p01) + 1e-5f * pd1;
+  } else {
+    const float4 b = X[v.y], c = X[v.z], d = X[v.w];
+    const float b0 = b.x - a.x, b1 = b.y - a.y, b2 = b.z - a.z;
+    const float c0 = c.x - a.x, c1 = c.y - a.y, c2 = c.z - a.z;
+    const float d0 = d.x - a.x, d1 = d.y - a.y, d2 = d.z - a.z;
+    const float B0 = f32_up(b0, eta), B1 = f32_up(b1, eta), B2 = f32_up(b2, eta);
+    const float C0 = f32_up(c0, eta), C1 = f32_up(c1, eta), C2 = f32_up(c2, eta);
+    const float D0 = f32_up(d0, eta), D1 = f32_up(d1, eta), D2 = f32_up(d2, eta);
+    const float lb = b0 * b0 + b1 * b1 + b2 * b2, lc = c0 * c0 + c1 * c1 + c2 * c2, ld = d0 * d0 + d1 * d1 + d2 * d2;
+    const float LB = B0 * B0 + B1 * B1 + B2 * B2, LC = C0 * C0 + C1 * C1 + C2 * C2, LD = D0 * D0 + D1 * D1 + D2 * D2;
+    const float cd[3] = {c1 * d2 - c2 * d1, c2 * d0 - c0 * d2, c0 * d1 - c1 * d0};
+    const float db[3] = {d1 * b2 - d2 * b1, d2 * b0 - d0 * b2, d0 * b1 - d1 * b0};
+    const float bc[3] = {b1 * c2 - b2 * c1, b2 * c0 - b0 * c2, b0 * c1 - b1 * c0};
+    const float pcd[3] = {fabsf(c1 * d2) + fabsf(c2 * d1), fabsf(c2 * d0) + fabsf(c0 * d2), fabsf(c0 * d1) + fabsf(c1 * d0)};
+    const float pdb[3] = {fabsf(d1 * b2) + fabsf(d2 * b1), fabsf(d2 * b0) + fabsf(d0 * b2), fabsf(d0 * b1) + fabsf(d1 * b0)};
+    const float pbc[3] = {fabsf(b1 * c2) + fabsf(b2 * c1), fabsf(b2 * c0) + fabsf(b0 * c2), fabsf(b0 * c1) + fabsf(b1 * c0)};
+    const float PCD[3] = {C1 * D2 + C2 * D1, C2 * D0 + C0 * D2, C0 * D1 + C1 * D0};
+    const float PDB[3] = {D1 * B2 + D2 * B1, D2 * B0 + D0 * B2, D0 * B1 + D1 * B0};
+    const float PBC[3] = {B1 * C2 + B2 * C1, B2 * C0 + B0 * C2, B0 * C1 + B1 * C0};
+    det = b0 * cd[0] + b1 * cd[1] + b2 * cd[2];
+    const float p0d = fabsf(b0) * pcd[0] + fabsf(b1) * pcd[1] + fabsf(b2) * pcd[2];
+    pdd = B0 * PCD[0] + B1 * PCD[1] + B2 * PCD[2];
+    Edet = (pdd - p0d) + 1e-5f * pdd;
+    for (int j = 0; j < 3; j++) {
+      N[j] = lb * cd[j] + lc * db[j] + ld * bc[j];
+      const float p0 = lb * pcd[j] + lc * pdb[j] + ld * pbc[j];
+      const float pd = LB * PCD[j] + LC * PDB[j] + LD * PBC[j];
+      EN[j] = (pd - p0) + 1e-5f * pd;
+    }
+  }
+  if (!(pdd > F32_TINY && pdd < F32_HUGE) || !(fabsf(det) > 4.0f * Edet)) return false;
+  const float adet = fabsf(det), inv = 0.5f / det;
+  float r2 = 0, e2 = 0, cc[3] = {0, 0, 0};
+  for (int j = 0; j < D; j++) {
+    cc[j] = N[j] * inv;
+    float e = 0.5f * (fabsf(N[j]) * Edet + adet * EN[j]) / (adet * (adet - Edet));
+    e += 4e-7f * fabsf(cc[j]);
+    r2 += cc[j] * cc[j];
+    e2 += e * e;
+  }
+  const float r = sqrtf(r2), err = sqrtf(e2);
+  if (!isfinite(r) || !isfinite(err)) return false;
+  double cmag = 0;
+  for (int j = 0; j < D; j++) {
+    const double x = j == 0 ? a.x : (j == 1 ? a.y : a.z);
+    S.c[j] = o[j] + (x + (double)cc[j]);
+    cmag = fmax(cmag, fabs(S.c[j]));
+  }
+  for (int j = D; j < 3; j++) S.c[j] = 0;
+  S.r = ((double)r * (1.0 + 1e-6) + 2.0 * (double)err * (1.0 + 1e-6) + (double)eta) * (1.0 + 1e-8) + 1e-14 * (1.0 + cmag);
+  S.half = false;
+  S.n[0] = S.n[1] = S.n[2] = 0;
+  S.pn[0] = S.pn[1] = S.pn[2] = 0;
+  return true;
+}
+
 // Halfspace beyond a ghost's hull facet: orient(ghost with the infinite
 // vertex replaced by x) >= 0, written as n.(x - a) >= -slack.
 template <int D>
@@ -322,6 +479,8 @@ __device__ void ghost_halfspace(const typename PT<D>::T* P, const int4& v, int g
 }
 
 struct BorderArgs {
+  const float4* xs;        // FP32 copies of the points (one frame: origin xo, bound in w)
+  const double* xo;
   const int4* tv;
   const int* toff;
   const int* tcount;
@@ -355,6 +514,8 @@ __global__ void k_border(const typename PT<D>::T* P, BorderArgs A) {
   if (g >= 0) {
     ghost_halfspace<D>(P, v, g, S);
     hit = A.prim == DT_PRIM_GRID ? grid_query<D>(A.G, S, others) : bbox_query<D>(A.boxes, A.k, S, others, i);
+  } else if (A.prim == DT_PRIM_GRID && circumball_f32<D>(A.xs, A.xo, v, S) && !grid_query<D>(A.G, S, others)) {
+    hit = false;   // even the larger FP32 ball meets no other partition
   } else if (!circumball<D>(P, v, S)) {
     hit = true;
   } else {
@@ -370,18 +531,6 @@ __global__ void k_border(const typename PT<D>::T* P, BorderArgs A) {
 __global__ void k_flag_bad_partitions(const int* pinst, const int* inst_status, int64_t n, unsigned char* vflag) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n && inst_status[pinst[i]] != 0) vflag[i] = 1;
-}
-
-template <int D>
-__global__ void k_part_boxes(const typename PT<D>::T* P, const int* pinst, int64_t n, unsigned long long* ubox) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int l = pinst[i];
-  for (int c = 0; c < D; c++) {
-    unsigned long long key = orderable_key(comp(P[i], c));
-    atomicMin(&ubox[6 * l + c], key);
-    atomicMax(&ubox[6 * l + 3 + c], key);
-  }
 }
 
 __global__ void k_boxes_to_double(const unsigned long long* ubox, int k, double* box) {
@@ -408,7 +557,15 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
   CUDA_OK(cudaMemsetAsync(cnt, 0, 16, s));
   unsigned g = (unsigned)ceil_div<int64_t>(n, 256);
   k_flag_bad_partitions<<<g, 256, (++c->launches, 0), s>>>(pinst, parts.inst_status, n, vflag);
+  // FP32 copies in one frame for the exclusion stage
+  float4* xs = nullptr;
+  const double* xo = nullptr;
+  std::vector<unsigned long long> hu;
+  int rc = fp32_points(c, dim, Ps, nullptr, n, 1, "b.xs", &xs, &hu, &xo);
+  if (rc) return rc;
   BorderArgs A;
+  A.xs = xs;
+  A.xo = xo;
   A.tv = (const int4*)parts.tv;
   A.toff = parts.toff;
   A.tcount = parts.tcount;
@@ -424,9 +581,9 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
   memset(&A.G, 0, sizeof(A.G));
   // per-partition boxes (bbox primitive and the grid's extent)
   CUDA_OK(cudaMemsetAsync(ubox, 0, 8 * 6 * (size_t)k, s));
-  k_init_ubox<<<ceil_div(6 * k, 128), 128, (++c->launches, 0), s>>>(ubox, k);
-  if (dim == 2) k_part_boxes<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)Ps, pinst, n, ubox);
-  else k_part_boxes<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)Ps, pinst, n, ubox);
+  k_box_init<<<ceil_div(6 * k, 128), 128, (++c->launches, 0), s>>>(ubox, k);
+  if (dim == 2) k_box_reduce<2><<<box_grid(n), 256, (++c->launches, 0), s>>>((const double2*)Ps, pinst, n, ubox);
+  else k_box_reduce<3><<<box_grid(n), 256, (++c->launches, 0), s>>>((const double4_32a*)Ps, pinst, n, ubox);
   k_boxes_to_double<<<ceil_div(6 * k, 128), 128, (++c->launches, 0), s>>>(ubox, k, boxes);
   if (prim == DT_PRIM_GRID) {
     if (k > 64) return set_err(c, DT_E_ARG, "the grid primitive supports k <= 64");
@@ -476,6 +633,7 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
       if (maxd <= 2) { lev++; break; }
     }
     G.levels = lev;
+    G.inv_h0 = 1.0 / G.h[0];
     for (int cc = 0; cc < 3; cc++) G.lo[cc] = cc < dim ? lo[cc] : 0.0;
     unsigned long long* mask = (unsigned long long*)pool_get(c, "b.mask", 8 * (size_t)total);
     if (!mask) return set_err(c, DT_E_NOMEM, "grid masks");
@@ -489,6 +647,15 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
       if (dim == 2) k_pyramid<2><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask);
       else k_pyramid<3><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask);
     }
+    unsigned long long* dil = (unsigned long long*)pool_get(c, "b.dil", 8 * (size_t)total);
+    if (!dil) return set_err(c, DT_E_NOMEM, "grid masks");
+    for (int l = 0; l < G.levels; l++) {
+      long long cells = (long long)G.dims[l][0] * G.dims[l][1] * G.dims[l][2];
+      unsigned gl = (unsigned)ceil_div<long long>(cells, 256);
+      if (dim == 2) k_dilate_mask<2><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask, dil);
+      else k_dilate_mask<3><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask, dil);
+    }
+    G.dil = dil;
   }
   unsigned gs = (unsigned)ceil_div<int64_t>(parts.total_slots, 128);
   if (dim == 2) k_border<2><<<gs, 128, (++c->launches, 0), s>>>((const double2*)Ps, A);

@@ -75,7 +75,7 @@ void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops
 
 // FP32 copies of the points for the first predicate stage (engine.cu).
 int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t npts, int ninst, const std::string& tag,
-                float4** xs_out, std::vector<unsigned long long>* hu_out);
+                float4** xs_out, std::vector<unsigned long long>* hu_out, const double** xo_out = nullptr);
 
 // Engine (engine.cu).
 int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,

@@ -11,6 +11,7 @@
 // Both end with a stable counting sort of the points by label.
 #include <cmath>
 
+#include "bbox.cuh"
 #include "divide.cuh"
 #include "pipeline.cuh"
 #include "sort.cuh"
@@ -536,9 +537,12 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
   int64_t m = G.eta;
   // start grid over the bounding box of all points, about m/4 cells
   double* box = (double*)pool_get(c, "lw.box", 48);
-  if (!box) return set_err(c, DT_E_NOMEM, "label box");
-  if (dim == 2) k_bbox<2><<<1, 256, (++c->launches, 0), s>>>((const double2*)P, n, box);
-  else k_bbox<3><<<1, 256, (++c->launches, 0), s>>>((const double4_32a*)P, n, box);
+  unsigned long long* ub = (unsigned long long*)pool_get(c, "lw.ubox", 48);
+  if (!box || !ub) return set_err(c, DT_E_NOMEM, "label box");
+  k_box_init<<<1, 32, (++c->launches, 0), s>>>(ub, 1);
+  if (dim == 2) k_box_reduce<2><<<box_grid(n), 256, (++c->launches, 0), s>>>((const double2*)P, nullptr, n, ub);
+  else k_box_reduce<3><<<box_grid(n), 256, (++c->launches, 0), s>>>((const double4_32a*)P, nullptr, n, ub);
+  k_box_to_double<<<1, 32, (++c->launches, 0), s>>>(ub, 1, dim, box);
   double hb[6];
   CUDA_OK(cudaMemcpyAsync(hb, box, 48, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "bbox.cuh"
 #include "sort.cuh"
 
 namespace gdt {
@@ -331,20 +332,25 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
   int nnom = min(*nnom_p, S.cap);
   constexpr int PER = 32 / (D + 1);
   // the region list lives in shared memory while it fits (copied out at the end)
+  // together with the neighbour links of each region simplex (loaded when the
+  // simplex joins, beside its claims, instead of one step later)
   constexpr int SHC = 128;
   __shared__ int s_region[4][SHC];
+  __shared__ int4 s_links[4][SHC];
   const bool in_shared = S.capC <= SHC && blockDim.x <= 128;
   for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < nnom; slot += nwarp) {
     int p = nominee_at(nom, bcnt, S.cap, slot);
     unsigned long long key = mkkey(round, p);
     int* Cg = S.cav + (int64_t)slot * S.capC;
     int* C = in_shared ? s_region[threadIdx.x >> 5] : Cg;
+    int4* NB = in_shared ? s_links[threadIdx.x >> 5] : nullptr;
     int* B = S.bnd + (int64_t)slot * S.capB;
     int t0 = T.loc[p];
     int status = CAND_OK;
     unsigned long long pbytes = 0, ptests = 0;
     if (lane == 0) {
       S.cand[slot] = p;
+      if (NB) NB[0] = T.tn[t0];
       unsigned long long o = atomicMax(&T.claimA[t0], key);
       if (o > key) status = CAND_LOST;
       C[0] = t0;
@@ -359,9 +365,10 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
       bool valid = lane < PER * (D + 1) && j < nc0;
       bool addC = false, addB = false, lost = false, bad = false;
       int t = -1, u = -1;
+      int4 links = make_int4(0, 0, 0, 0);
       if (valid) {
         t = C[j];
-        u = nb_simplex(*comp_ptr(T.tn, t, i));
+        u = nb_simplex(NB ? get4(NB[j], i) : *comp_ptr(T.tn, t, i));
         if (!slot_ok(T, u)) {
           bad = true;
         } else {
@@ -380,6 +387,7 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
               if (in_conflict_x(T.pts, T.xs, T.gid, vt, p, D)) {
                 // both claims at once; the region claim decides, the ring claim
                 // can only raise claimA to a key that is no stronger than needed
+                if (NB) links = T.tn[u];                   // in flight beside the two claims
                 unsigned long long o = atomicMax(&T.claimC[u], key);
                 unsigned long long o2 = atomicMax(&T.claimA[u], key);
                 if (o > key || o2 > key) {
@@ -403,7 +411,10 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
       int nC = __popc(mC), nB = __popc(mB);
       if (nc + nC > S.capC || nbd + nB > S.capB) { status = CAND_OVER; break; }
       unsigned lt = (1u << lane) - 1;
-      if (addC) C[nc + __popc(mC & lt)] = u;
+      if (addC) {
+        C[nc + __popc(mC & lt)] = u;
+        if (NB) NB[nc + __popc(mC & lt)] = links;
+      }
       if (addB) B[nbd + __popc(mB & lt)] = pack_nb(t, i);
       nc += nC;
       nbd += nB;
@@ -714,22 +725,6 @@ __device__ __forceinline__ unsigned long long ord_key(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x + 0.0);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
-__global__ void k_ubox_init(unsigned long long* ub, int ninst) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 6 * ninst) ub[i] = (i % 6) < 3 ? ~0ull : 0ull;
-}
-template <int D>
-__global__ void k_inst_bbox(const typename PT<D>::T* pts, const int* pinst, int64_t npts, unsigned long long* ub) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= npts) return;
-  int i = pinst ? pinst[p] : 0;
-  for (int c = 0; c < D; c++) {
-    unsigned long long k = ord_key(comp(pts[p], c));
-    atomicMin(&ub[6 * i + c], k);
-    atomicMax(&ub[6 * i + 3 + c], k);
-  }
-}
-
 // FP32 copies for the first predicate stage: X = fl32(x - o_i), w = eta_i
 // (xo: per instance the origin (3) and eta (1)).
 template <int D>
@@ -858,20 +853,21 @@ int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool 
 // rounded up, R the largest |x_c - o_c|.  *hu_out receives the boxes as
 // orderable keys (lo[3], hi[3] per instance).
 int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t npts, int ninst, const std::string& tag,
-                float4** xs_out, std::vector<unsigned long long>* hu_out) {
+                float4** xs_out, std::vector<unsigned long long>* hu_out, const double** xo_out) {
   cudaStream_t s = c->stream;
   float4* xs = (float4*)pool_get(c, tag, 16 * (size_t)std::max<int64_t>(npts, 1));
   double* xo = (double*)pool_get(c, tag + ".o", 8 * 4 * (size_t)ninst);
   unsigned long long* ub = (unsigned long long*)pool_get(c, tag + ".box", 8 * 6 * (size_t)ninst);
   if (!xs || !xo || !ub) return set_err(c, DT_E_NOMEM, "fp32 points");
   *xs_out = xs;
+  if (xo_out) *xo_out = xo;
   std::vector<unsigned long long>& hu = *hu_out;
   hu.assign(6 * (size_t)ninst, 0);
   if (npts == 0) return 0;
   unsigned g = (unsigned)ceil_div<int64_t>(npts, 256);
-  k_ubox_init<<<ceil_div(6 * ninst, 128), 128, (++c->launches, 0), s>>>(ub, ninst);
-  if (dim == 2) k_inst_bbox<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)pts, pinst, npts, ub);
-  else k_inst_bbox<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)pts, pinst, npts, ub);
+  k_box_init<<<ceil_div(6 * ninst, 128), 128, (++c->launches, 0), s>>>(ub, ninst);
+  if (dim == 2) k_box_reduce<2><<<box_grid(npts), 256, (++c->launches, 0), s>>>((const double2*)pts, pinst, npts, ub);
+  else k_box_reduce<3><<<box_grid(npts), 256, (++c->launches, 0), s>>>((const double4_32a*)pts, pinst, npts, ub);
   CUDA_OK(cudaMemcpyAsync(hu.data(), ub, 8 * 6 * (size_t)ninst, cudaMemcpyDeviceToHost, s));
   CUDA_OK(cudaStreamSynchronize(s));
   std::vector<double> hxo(4 * (size_t)ninst, 0.0);
