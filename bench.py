@@ -280,15 +280,18 @@ def run_serving(args, w):
                  "p99_ms": float(np.percentile(lat, 99) * 1e3), "capacity_mpts": cap / 1e6}
     jobs = [Job(float(arr[i]), i, pts[i], k=k_for(len(pts[i])), frac=w["frac"]) for i in range(len(pts))]
     srv = Server(device=local, workers=3, budget_bytes=120e9, bytes_per_point=6000.0, keep_results=False)
+    clk = ClockSampler(local)
+    clk.start()
     served = srv.run(jobs)
+    clocks = clk.stop()
     line = {"metric": METRIC, "value": served["throughput_mpts"], "unit": "Mpoints/s", "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": served["makespan_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "jobs": len(pts), "points": total, "offered_load": w["load"],
                        "budget_gb": 120, "workers": 3},
-            "serve": {"served": served, "plain": plain_sum},
+            "serve": {"served": served, "plain": plain_sum}, "clocks": clocks, "gpu_launches": served["launches"],
             "e2e": {"value": served["throughput_mpts"], "unit": "Mpoints/s",
-                    "h2d_bytes_per_step": total * 24, "d2h_bytes_per_step": None}}
+                    "h2d_bytes_per_step": total * 24, "d2h_bytes_per_step": int(served["rows_out"]) * 16}}
     print(json.dumps(line), flush=True)
     return 0
 

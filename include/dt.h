@@ -89,7 +89,9 @@ typedef struct dt_config {
   int neighbors;         /* 1: run the neighbourhood update inside dt_triangulate (otherwise it runs
                             on the first dt_get_neighbors call) */
   int first_batch;       /* points per instance in the first insertion batch (BRIO); 0 = automatic (32) */
-  int reserved[5];
+  int brio_growth;       /* BRIO batch growth x 100: each batch has about (growth - 1) times the points
+                            inserted before it; 0 = automatic (150) */
+  int reserved[4];
 } dt_config;
 
 typedef struct dt_stats {

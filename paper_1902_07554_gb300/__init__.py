@@ -48,7 +48,8 @@ class Config(ctypes.Structure):
                 ("grid_cell", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("base_threshold", ctypes.c_int), ("validate", ctypes.c_int),
                 ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
-                ("first_batch", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("first_batch", ctypes.c_int), ("brio_growth", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class KernelProfile(ctypes.Structure):

@@ -11,6 +11,7 @@ struct dt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;     // capture stream of the insertion-round graph
+  bool pdl_ok = true;                    // programmatic launches accepted in the round graph
   bool own_stream = false;
   dt_config cfg;
   std::string err;

@@ -16,9 +16,12 @@ constexpr int TAGBIT = (int)0x80000000;
 // Candidate key of point p in a round: the round in the high word (older
 // claims compare smaller), a per-round pseudo-random priority in the low word
 // (p -> p ^ c and fmix32 are bijections, so keys are unique within a round).
+// Round key of point p: (round, hash of p and round, pass bit).  The pass bit
+// is set when a large region is grown a second time (k_cavity_big): the
+// nominee then outranks its own first-pass claims but no other nominee.
 __device__ __forceinline__ unsigned long long mkkey(unsigned round, int p) {
-  return ((unsigned long long)round << 32) |
-         (unsigned long long)fmix32((uint32_t)p ^ (round * 0x9E3779B9u));
+  return ((unsigned long long)round << 33) |
+         ((unsigned long long)fmix32((uint32_t)p ^ (round * 0x9E3779B9u)) << 1);
 }
 __device__ __forceinline__ int get4(const int4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -100,6 +103,10 @@ __device__ __forceinline__ int orient_tuple(const TriView<D>& T, const int4& v) 
 // One thread per instance: the first D+1 affinely independent points (in
 // index order) form a positively oriented simplex, surrounded by D+1 ghost
 // simplices (infinite vertex + one hull facet each).
+constexpr int NLEV = 96;   // activation levels (BRIO batches)
+constexpr int BIGCAP = 256;      // large regions grown per round
+constexpr int BIG_C = 16384, BIG_B = 32768;   // their list capacities
+
 // Round state of the device-driven insertion loop (a CUDA graph whose
 // conditional WHILE node repeats one round: begin, activate, nominate,
 // cavity, insert, relocate, end).  The kernels take their round, active lists
@@ -117,6 +124,16 @@ struct EngCtl {
   int activated;       // points activated this round
   int done;            // 0 running; 1 finished; 2 device error; 3 stalled; 4 round limit
 };
+
+// Programmatic dependent launch inside the round graph: each round kernel
+// first waits for the kernel before it to complete (griddepcontrol.wait: its
+// memory is then visible), then lets the next one start launching, so that
+// the next launch overlaps this kernel's run.  Both are no-ops in a launch
+// without the programmatic attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+}
 
 template <int D>
 __global__ void k_init(TriView<D> T, int ninst, const long long* poff, const int* toff, int* inst_status) {
@@ -189,12 +206,17 @@ __global__ void k_init(TriView<D> T, int ninst, const long long* poff, const int
 // (a randomized insertion order with a growing prefix, as in biased randomized
 // insertion orders).  -1: not to be inserted (initial simplex / bad instance).
 template <int D>
-__global__ void k_levels(TriView<D> T, int64_t npts, const int* inst_status, int* level) {
+__global__ void k_levels(TriView<D> T, int64_t npts, const int* inst_status, int* level, float inv_log2_growth) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npts) return;
   int l = -1;
-  if (inst_status[T.pinst[p]] == 0 && T.state[p] == 0)
-    l = __clz((int)fmix32((uint32_t)T.gid[p] * 0x9E3779B1u + 0x7F4A7C15u));
+  if (inst_status[T.pinst[p]] == 0 && T.state[p] == 0) {
+    // P(level >= l) = growth^-l: activating the levels from the top, each
+    // batch is about (growth - 1) times the points activated before it
+    const uint32_t h = fmix32((uint32_t)T.gid[p] * 0x9E3779B1u + 0x7F4A7C15u);
+    const float u = ((float)(h >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    l = min(NLEV - 1, (int)(-__log2f(u) * inv_log2_growth));
+  }
   level[p] = l;
 }
 
@@ -245,7 +267,7 @@ enum { CAND_OK = 0, CAND_LOST = 1, CAND_OVER = 2 };
 // nominees are claimed early and weaker ones stop at their first contact.
 constexpr int NBUCKET = 8;
 __device__ __forceinline__ int key_bucket(unsigned long long key) {
-  return NBUCKET - 1 - (int)((uint32_t)key >> 29);
+  return NBUCKET - 1 - (int)((key >> 30) & 7);   // the top 3 bits of the hash
 }
 
 // Slot -> nominee: slots enumerate the buckets in order (bcnt: bucket sizes,
@@ -265,6 +287,7 @@ __device__ __forceinline__ int nominee_at(const int* nom, const int* bcnt, int s
 template <int D>
 __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, const int* nact_p, unsigned round,
                                                   int* nom, int* nnom, int* bcnt, int seg, const EngCtl* ctl) {
+  pdl_enter();
   __shared__ int s_cnt[NBUCKET], s_base[NBUCKET];
   if (ctl) { act = ctl->ain; round = ctl->round; }
   const int nact = *nact_p;
@@ -322,15 +345,129 @@ __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, 
 // step.  Conflicting neighbours join the region (claimC/claimA atomicMax; the
 // returned old value also deduplicates lanes that reach the same simplex),
 // the others become boundary facets (ring claim in claimA).
+// One warp grows nominee p's conflict region into C (region simplices; NB:
+// optional copies of their links) and B (boundary facets), claiming as it
+// goes.  status: CAND_OK, CAND_LOST (met a stronger claim) or CAND_OVER (the
+// lists are full).
+template <int D>
+__device__ __forceinline__ void grow_region(const TriView<D>& T, int p, unsigned long long key, int* C, int4* NB, int* B,
+                                            int capC, int capB, int& nc_out, int& nbd_out, int& status_out,
+                                            unsigned long long& pbytes, unsigned long long& ptests) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  constexpr int PER = 32 / (D + 1);
+  int t0 = T.loc[p];
+  int status = CAND_OK;
+  if (lane == 0) {
+    if (NB) NB[0] = T.tn[t0];
+    // the located simplex carries p's pick (= key) already, except on a second
+    // pass (key has its pass bit): claim it in both words so that no lane adds
+    // it to the region a second time
+    unsigned long long oc = atomicMax(&T.claimC[t0], key);
+    unsigned long long o = atomicMax(&T.claimA[t0], key);
+    if (o > key || oc > key) status = CAND_LOST;
+    C[0] = t0;
+    pbytes += sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1) + 16 + 4;
+  }
+  status = __shfl_sync(FULL, status, 0);
+  int nc = 1, nbd = 0;
+  __syncwarp();
+  for (int h = 0; h < nc && status == CAND_OK;) {
+    const int nc0 = nc;                                // region simplices known at this step
+    int j = h + lane / (D + 1), i = lane % (D + 1);
+    bool valid = lane < PER * (D + 1) && j < nc0;
+    bool addC = false, addB = false, lost = false, bad = false;
+    int t = -1, u = -1;
+    int4 links = make_int4(0, 0, 0, 0);
+    if (valid) {
+      t = C[j];
+      u = nb_simplex(NB ? get4(NB[j], i) : *comp_ptr(T.tn, t, i));
+      if (!slot_ok(T, u)) {
+        bad = true;
+      } else {
+        const int4 vv = T.tv[u];                       // loaded beside the claim, not after it
+        unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
+        pbytes += 16;
+        if (cC > key) {
+          lost = true;                                 // inside a stronger region
+        } else if (cC != key) {
+          pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
+          ptests++;
+          if (!verts_ok(T, vv)) {
+            bad = true;
+          } else {
+            int vt[4] = {vv.x, vv.y, vv.z, vv.w};
+            if (in_conflict_x(T.pts, T.xs, T.gid, vt, p, D)) {
+              // both claims at once; the region claim decides, the ring claim
+              // can only raise claimA to a key that is no stronger than needed
+              if (NB) links = T.tn[u];                   // in flight beside the two claims
+              unsigned long long o = atomicMax(&T.claimC[u], key);
+              unsigned long long o2 = atomicMax(&T.claimA[u], key);
+              if (o > key || o2 > key) {
+                lost = true;
+              } else if (o < key) {                    // first lane to claim it
+                addC = true;
+                pbytes += 16 + 16 + 4;
+              }
+            } else {
+              atomicMax(&T.claimA[u], key);
+              addB = true;
+              pbytes += 8 + 4;
+            }
+          }
+        }
+      }
+    }
+    if (bad) set_error(T.st, DT_E_INTERNAL, 10);
+    if (__any_sync(FULL, lost || bad)) { status = CAND_LOST; break; }
+    unsigned mC = __ballot_sync(FULL, addC), mB = __ballot_sync(FULL, addB);
+    int nC = __popc(mC), nB = __popc(mB);
+    if (nc + nC > capC || nbd + nB > capB) { status = CAND_OVER; break; }
+    unsigned lt = (1u << lane) - 1;
+    if (addC) {
+      C[nc + __popc(mC & lt)] = u;
+      if (NB) NB[nc + __popc(mC & lt)] = links;
+    }
+    if (addB) B[nbd + __popc(mB & lt)] = pack_nb(t, i);
+    nc += nC;
+    nbd += nB;
+    h = min(h + PER, nc0);                             // simplices appended now come next
+    __syncwarp();
+  }
+  nc_out = nc;
+  nbd_out = nbd;
+  status_out = status;
+}
+
+template <int D>
+__device__ __forceinline__ void region_stats(const TriView<D>& T, int status, int nc, unsigned long long pbytes,
+                                             unsigned long long ptests) {
+  const unsigned FULL = 0xffffffffu;
+  if (T.prof) {
+    for (int off = 16; off; off >>= 1) {
+      pbytes += __shfl_down_sync(FULL, pbytes, off);
+      ptests += __shfl_down_sync(FULL, ptests, off);
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (T.dbg) {   // [4] complete regions, [5] region simplices grown by all nominees, [6] large regions
+      if (status == CAND_OK) atomicAdd(&T.dbg[4], 1ull);
+      atomicAdd(&T.dbg[5], (unsigned long long)nc);
+    }
+    if (T.prof) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
+  }
+}
+
+// One warp per nominee, strongest list first.  A region that outgrows the
+// regular lists is queued for k_cavity_big (up to BIGCAP per round).
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
                                                   CandScratch S, const int* bcnt, const EngCtl* ctl) {
-  const unsigned FULL = 0xffffffffu;
+  pdl_enter();
   if (ctl) round = ctl->round;
   int lane = threadIdx.x & 31;
   int nwarp = (gridDim.x * blockDim.x) >> 5;
   int nnom = min(*nnom_p, S.cap);
-  constexpr int PER = 32 / (D + 1);
   // the region list lives in shared memory while it fits (copied out at the end)
   // together with the neighbour links of each region simplex (loaded when the
   // simplex joins, beside its claims, instead of one step later)
@@ -345,98 +482,49 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
     int* C = in_shared ? s_region[threadIdx.x >> 5] : Cg;
     int4* NB = in_shared ? s_links[threadIdx.x >> 5] : nullptr;
     int* B = S.bnd + (int64_t)slot * S.capB;
-    int t0 = T.loc[p];
-    int status = CAND_OK;
+    if (lane == 0) S.cand[slot] = p;
     unsigned long long pbytes = 0, ptests = 0;
-    if (lane == 0) {
-      S.cand[slot] = p;
-      if (NB) NB[0] = T.tn[t0];
-      unsigned long long o = atomicMax(&T.claimA[t0], key);
-      if (o > key) status = CAND_LOST;
-      C[0] = t0;
-      pbytes += sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1) + 16 + 4;
-    }
-    status = __shfl_sync(FULL, status, 0);
-    int nc = 1, nbd = 0;
-    __syncwarp();
-    for (int h = 0; h < nc && status == CAND_OK;) {
-      const int nc0 = nc;                                // region simplices known at this step
-      int j = h + lane / (D + 1), i = lane % (D + 1);
-      bool valid = lane < PER * (D + 1) && j < nc0;
-      bool addC = false, addB = false, lost = false, bad = false;
-      int t = -1, u = -1;
-      int4 links = make_int4(0, 0, 0, 0);
-      if (valid) {
-        t = C[j];
-        u = nb_simplex(NB ? get4(NB[j], i) : *comp_ptr(T.tn, t, i));
-        if (!slot_ok(T, u)) {
-          bad = true;
-        } else {
-          const int4 vv = T.tv[u];                       // loaded beside the claim, not after it
-          unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
-          pbytes += 16;
-          if (cC > key) {
-            lost = true;                                 // inside a stronger region
-          } else if (cC != key) {
-            pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
-            ptests++;
-            if (!verts_ok(T, vv)) {
-              bad = true;
-            } else {
-              int vt[4] = {vv.x, vv.y, vv.z, vv.w};
-              if (in_conflict_x(T.pts, T.xs, T.gid, vt, p, D)) {
-                // both claims at once; the region claim decides, the ring claim
-                // can only raise claimA to a key that is no stronger than needed
-                if (NB) links = T.tn[u];                   // in flight beside the two claims
-                unsigned long long o = atomicMax(&T.claimC[u], key);
-                unsigned long long o2 = atomicMax(&T.claimA[u], key);
-                if (o > key || o2 > key) {
-                  lost = true;
-                } else if (o < key) {                    // first lane to claim it
-                  addC = true;
-                  pbytes += 16 + 16 + 4;
-                }
-              } else {
-                atomicMax(&T.claimA[u], key);
-                addB = true;
-                pbytes += 8 + 4;
-              }
-            }
-          }
-        }
-      }
-      if (bad) set_error(T.st, DT_E_INTERNAL, 10);
-      if (__any_sync(FULL, lost || bad)) { status = CAND_LOST; break; }
-      unsigned mC = __ballot_sync(FULL, addC), mB = __ballot_sync(FULL, addB);
-      int nC = __popc(mC), nB = __popc(mB);
-      if (nc + nC > S.capC || nbd + nB > S.capB) { status = CAND_OVER; break; }
-      unsigned lt = (1u << lane) - 1;
-      if (addC) {
-        C[nc + __popc(mC & lt)] = u;
-        if (NB) NB[nc + __popc(mC & lt)] = links;
-      }
-      if (addB) B[nbd + __popc(mB & lt)] = pack_nb(t, i);
-      nc += nC;
-      nbd += nB;
-      h = min(h + PER, nc0);                             // simplices appended now come next
-      __syncwarp();
-    }
+    int nc, nbd, status;
+    grow_region<D>(T, p, key, C, NB, B, S.capC, S.capB, nc, nbd, status, pbytes, ptests);
     if (in_shared && status == CAND_OK)
       for (int q = lane; q < nc; q += 32) Cg[q] = C[q];
-    if (T.prof) {
-      for (int off = 16; off; off >>= 1) {
-        pbytes += __shfl_down_sync(FULL, pbytes, off);
-        ptests += __shfl_down_sync(FULL, ptests, off);
+    region_stats<D>(T, status, nc, pbytes, ptests);
+    if (lane == 0) {
+      if (status == CAND_OVER) {
+        if (T.dbg) atomicAdd(&T.dbg[6], 1ull);
+        const int q = atomicAdd(S.nbig, 1);
+        if (q < BIGCAP) S.biglist[q] = slot;
+        else atomicExch(&T.st->overflow_cav, 1);
       }
+      S.meta[slot] = make_int4(nc, nbd, status, 0);
     }
+    __syncwarp();
+  }
+}
+
+// Large regions: the nominees whose region outgrew the regular lists grow it
+// again into lists of capCbig / capBbig entries (their claims so far stand;
+// atomicMax makes the repeated claims harmless).
+template <int D>
+__global__ void __launch_bounds__(128) k_cavity_big(TriView<D> T, unsigned round, CandScratch S, const EngCtl* ctl) {
+  pdl_enter();
+  if (ctl) round = ctl->round;
+  const int lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int nbig = min(*S.nbig, BIGCAP);
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nbig; q += nwarp) {
+    const int slot = S.biglist[q];
+    const int p = S.cand[slot];
+    const unsigned long long key = mkkey(round, p) | 1ull;   // second pass: see mkkey
+    int* C = S.bigcav + (int64_t)q * S.capCbig;
+    int* B = S.bigbnd + (int64_t)q * S.capBbig;
+    unsigned long long pbytes = 0, ptests = 0;
+    int nc, nbd, status;
+    grow_region<D>(T, p, key, C, nullptr, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
+    region_stats<D>(T, status, nc, pbytes, ptests);
     if (lane == 0) {
       if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
-      S.meta[slot] = make_int4(nc, nbd, status, 0);
-      if (T.dbg) {   // [4] complete regions, [5] region simplices grown by all nominees
-        if (status == CAND_OK) atomicAdd(&T.dbg[4], 1ull);
-        atomicAdd(&T.dbg[5], (unsigned long long)nc);
-      }
-      if (T.prof) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
+      S.meta[slot] = make_int4(nc, nbd, status, q + 1);
     }
     __syncwarp();
   }
@@ -448,6 +536,7 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
 template <int D>
 __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, CandScratch S, const int* nnom_p,
                                                   int* nwin, const EngCtl* ctl) {
+  pdl_enter();
   const unsigned FULL = 0xffffffffu;
   if (ctl) round = ctl->round;
   int lane = threadIdx.x & 31;
@@ -457,10 +546,11 @@ __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, 
     int4 m = S.meta[slot];
     if (m.z != CAND_OK) continue;
     int p = S.cand[slot];
-    unsigned long long key = mkkey(round, p);
-    const int* C = S.cav + (int64_t)slot * S.capC;
-    const int* B = S.bnd + (int64_t)slot * S.capB;
-    int* OUT = S.outer + (int64_t)slot * S.capB;
+    const bool big = m.w > 0;
+    const unsigned long long key = mkkey(round, p) | (big ? 1ull : 0ull);
+    const int* C = big ? S.bigcav + (int64_t)(m.w - 1) * S.capCbig : S.cav + (int64_t)slot * S.capC;
+    const int* B = big ? S.bigbnd + (int64_t)(m.w - 1) * S.capBbig : S.bnd + (int64_t)slot * S.capB;
+    int* OUT = big ? S.bigout + (int64_t)(m.w - 1) * S.capBbig : S.outer + (int64_t)slot * S.capB;
     int nc = m.x, nbd = m.y;
     bool ok = true;
     for (int j = lane; j < nc; j += 32)
@@ -600,6 +690,7 @@ __device__ int walk_to(const TriView<D>& T, int s, int p, int limit, int* steps_
 template <int D>
 __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, int* act_out, int* nact_out,
                               int* walk, int* nwalk, unsigned next_round, const EngCtl* ctl) {
+  pdl_enter();
   if (ctl) { act = ctl->ain; act_out = ctl->aout; next_round = ctl->round + 1; }
   const int nact = *nact_p;
   // warp-uniform grid-stride loop (warp_append needs every lane)
@@ -635,6 +726,7 @@ __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, i
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_activate(TriView<D> T, const int* list, int m, int* act, int* nact,
                                                   unsigned next_round, const EngCtl* ctl) {
+  pdl_enter();
   if (ctl) { list += ctl->act_lo; m = ctl->act_n; act = ctl->ain; next_round = ctl->round; }
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < m;
        base += (int64_t)gridDim.x * blockDim.x) {
@@ -704,6 +796,7 @@ __global__ void k_check_mesh(TriView<D> T, const int* toff, const int* tcount, i
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p,
                                                     unsigned next_round, const EngCtl* ctl) {
+  pdl_enter();
   if (ctl) next_round = ctl->round + 1;
   const int nwalk = *nwalk_p;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nwalk;
@@ -749,10 +842,8 @@ __global__ void k_move_count(int* dst, int* src) {
 
 // Start of a device-driven round: activate the next level(s) when the active
 // set has drained to a quarter of the last batch (the rule of the host
-// loop), advance the round, clear the round's counters.  One thread.
-__global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  EngCtl& C = *ctl;
+// loop), advance the round, clear the round's counters.
+__device__ void round_begin(EngCtl& C, int* cnt, const int* loffd) {
   int nact = cnt[0];
   int lo = -1, hi = -1;
   while (C.next_level >= 0 && nact <= C.last_batch / 4) {
@@ -770,16 +861,24 @@ __global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
   C.act_n = lo < 0 ? 0 : hi - lo;
   C.activated = C.act_n;
   if (nact > 0) C.round++;
-  if (C.round > 400000) C.done = 4;
-  cnt[1] = cnt[2] = cnt[3] = cnt[4] = 0;
+  if (C.round > 400000 && C.done == 0) C.done = 4;
+  cnt[1] = cnt[2] = cnt[3] = cnt[4] = cnt[5] = 0;
   for (int b = 0; b < NBUCKET; b++) cnt[8 + b] = 0;
 }
 
-// End of a device-driven round: the next active list becomes current; the
-// loop ends when nothing is left, on a device error, after 4 rounds in a row
-// without an insertion (a cavity overflowed its scratch: the host grows it),
-// or at the round limit.
-__global__ void k_round_end(EngCtl* ctl, int* cnt, const DevStatus* st, cudaGraphConditionalHandle handle) {
+// The first round's start (before the loop).  One thread.
+__global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  round_begin(*ctl, cnt, loffd);
+}
+
+// End of a device-driven round and start of the next: the next active list
+// becomes current; the loop ends when nothing is left, on a device error,
+// after 4 rounds in a row without an insertion (a cavity overflowed its
+// scratch: the host grows it), or at the round limit.  One thread.
+__global__ void k_round_step(EngCtl* ctl, int* cnt, const int* loffd, const DevStatus* st,
+                             cudaGraphConditionalHandle handle) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   EngCtl& C = *ctl;
   const int had = cnt[0];
@@ -796,6 +895,7 @@ __global__ void k_round_end(EngCtl* ctl, int* cnt, const DevStatus* st, cudaGrap
     else if (cnt[3] > 0) C.stalled = 0;
   }
   C.last_nact = nnew;
+  if (C.done == 0) round_begin(C, cnt, loffd);
   cudaGraphSetConditional(handle, C.done == 0 ? 1u : 0u);
 }
 
@@ -893,6 +993,19 @@ int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t n
   return 0;
 }
 
+// Scratch of the large regions (shared by every round; counter cnt[5]).
+static int big_scratch(dt_ctx* c, CandScratch& S, int* cnt) {
+  S.capCbig = BIG_C;
+  S.capBbig = BIG_B;
+  S.bigcav = (int*)pool_get(c, "eng.bigcav", 4 * (size_t)BIGCAP * BIG_C);
+  S.bigbnd = (int*)pool_get(c, "eng.bigbnd", 4 * (size_t)BIGCAP * BIG_B);
+  S.bigout = (int*)pool_get(c, "eng.bigout", 4 * (size_t)BIGCAP * BIG_B);
+  S.biglist = (int*)pool_get(c, "eng.biglist", 4 * (size_t)BIGCAP);
+  S.nbig = cnt + 5;
+  if (!S.bigcav || !S.bigbnd || !S.bigout || !S.biglist) return set_err(c, DT_E_NOMEM, "large-region scratch");
+  return 0;
+}
+
 // Capture stream of the context (created on first use).
 static cudaStream_t capture_stream(dt_ctx* c) {
   if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -946,6 +1059,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     S.outer = (int*)pool_get(c, "eng.outer", 4 * (size_t)capCand * S.capB);
     S.count = cnt + 2;
     if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
+    { int rcb = big_scratch(c, S, cnt); if (rcb) return rcb; }
     cudaGraph_t g = nullptr;
     cudaGraphExec_t gx = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
@@ -961,18 +1075,48 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      k_round_begin<<<1, 32, 0, cs>>>(ctl, cnt, loffd);
-      k_activate<D><<<ga, 128, 0, cs>>>(T, llist, 0, nullptr, cnt + 0, 0, ctl);
-      k_nominate<D><<<gn, 256, 0, cs>>>(T, nullptr, cnt + 0, 0, nom, cnt + 2, cnt + 8, capCand, ctl);
-      k_cavity_w<D><<<gw, 128, 0, cs>>>(T, nom, cnt + 2, 0, S, cnt + 8, ctl);
-      k_insert_w<D><<<gw, 128, 0, cs>>>(T, 0, S, cnt + 2, cnt + 3, ctl);
-      k_reloc_check<D><<<gn, 256, 0, cs>>>(T, nullptr, cnt + 0, nullptr, cnt + 1, walk, cnt + 4, 0, ctl);
-      k_reloc_walk<D><<<gr, 128, 0, cs>>>(T, walk, cnt + 4, 0, ctl);
-      k_round_end<<<1, 32, 0, cs>>>(ctl, cnt, c->status, hc);
+      // body: one round; programmatic edges let each launch overlap the kernel before it
+      const bool pdl = c->pdl_ok;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      auto cfg = [&](unsigned grid, unsigned block) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(grid);
+        lc.blockDim = dim3(block);
+        lc.stream = cs;
+        lc.attrs = pdl ? at : nullptr;
+        lc.numAttrs = pdl ? 1 : 0;
+        return lc;
+      };
+      cudaLaunchConfig_t l1 = cfg(ga, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128), l5 = cfg(gn, 256),
+                         l6 = cfg(gr, 128), l7 = cfg(1, 32), l8 = cfg(BIGCAP / 4, 128);
+      l1.numAttrs = 0;   // the body's first node has no kernel before it inside the body
+      cudaLaunchKernelEx(&l1, k_activate<D>, T, (const int*)llist, 0, (int*)nullptr, cnt + 0, 0u, (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, nom, cnt + 2, cnt + 8,
+                         capCand, (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l3, k_cavity_w<D>, T, (const int*)nom, (const int*)(cnt + 2), 0u, S, (const int*)(cnt + 8),
+                         (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l8, k_cavity_big<D>, T, 0u, S, (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l4, k_insert_w<D>, T, 0u, S, (const int*)(cnt + 2), cnt + 3, (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l5, k_reloc_check<D>, T, (const int*)nullptr, (const int*)(cnt + 0), (int*)nullptr, cnt + 1,
+                         walk, cnt + 4, 0u, (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l6, k_reloc_walk<D>, T, (const int*)walk, (const int*)(cnt + 4), 0u, (const EngCtl*)ctl);
+      cudaLaunchKernelEx(&l7, k_round_step, ctl, cnt, loffd, (const DevStatus*)c->status, hc);
       cudaGraph_t captured = nullptr;
       e = cudaStreamEndCapture(cs, &captured);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+    if (e != cudaSuccess && c->pdl_ok) {
+      // programmatic edges refused inside the loop body: capture again without them
+      cudaGetLastError();
+      if (gx) cudaGraphExecDestroy(gx);
+      if (g) cudaGraphDestroy(g);
+      c->pdl_ok = false;
+      grow--;
+      continue;
+    }
+    if (e == cudaSuccess) k_round_begin<<<1, 32, 0, s>>>(ctl, cnt, loffd);
     if (e == cudaSuccess) e = cudaGraphLaunch(gx, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (gx) cudaGraphExecDestroy(gx);
@@ -982,7 +1126,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     CUDA_OK(cudaMemcpyAsync(&h1, ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
-    c->launches += 1 + 8 * (int64_t)(h1.round - r0 + 1);
+    c->launches += 1 + 9 * (int64_t)(h1.round - r0 + 1);
     if (h1.done == 3 && c->status_host->overflow_cav && grow < 8) {
       // cavities outgrew their scratch: twice the room, same state
       CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));
@@ -1143,30 +1287,32 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     // activation levels and the per-level lists of dormant points
     int* level = (int*)pool_get(c, tag + ".level", 4 * std::max<int64_t>(npts, 1));
     int* lrank = (int*)pool_get(c, "eng.lrank", 4 * std::max<int64_t>(npts, 1));
-    int* lsize = (int*)pool_get(c, "eng.lsize", 4 * 64);
+    int* lsize = (int*)pool_get(c, "eng.lsize", 4 * (NLEV + 1));
     int* llist = (int*)pool_get(c, tag + ".llist", 4 * std::max<int64_t>(npts, 1));
-    int* loffd = (int*)pool_get(c, "eng.loff", 4 * 64);
+    int* loffd = (int*)pool_get(c, "eng.loff", 4 * (NLEV + 1));
     if (!level || !lrank || !lsize || !llist || !loffd) return set_err(c, DT_E_NOMEM, "activation levels");
-    std::vector<int64_t> loff(34, 0);
+    std::vector<int64_t> loff(NLEV + 1, 0);
     int first_level = 0;
     if (npts > 0) {
       unsigned gpp = (unsigned)ceil_div<int64_t>(npts, 256);
-      k_levels<D><<<gpp, 256, (++c->launches, 0), s>>>(T, npts, run.inst_status, level);
-      int rc = group_rank(c, level, npts, lrank, lsize, 33);
+      const double growth = c->cfg.brio_growth > 100 ? c->cfg.brio_growth / 100.0 : 1.5;
+      k_levels<D><<<gpp, 256, (++c->launches, 0), s>>>(T, npts, run.inst_status, level,
+                                                       (float)(1.0 / std::log2(growth)));
+      int rc = group_rank(c, level, npts, lrank, lsize, NLEV);
       if (rc) return rc;
-      int hs[33];
-      CUDA_OK(cudaMemcpyAsync(hs, lsize, 4 * 33, cudaMemcpyDeviceToHost, s));
+      int hs[NLEV];
+      CUDA_OK(cudaMemcpyAsync(hs, lsize, 4 * NLEV, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
-      for (int l = 0; l < 33; l++) loff[l + 1] = loff[l] + hs[l];
-      std::vector<int> lo32(34);
-      for (int l = 0; l < 34; l++) lo32[l] = (int)loff[l];
-      CUDA_OK(cudaMemcpyAsync(loffd, lo32.data(), 4 * 34, cudaMemcpyHostToDevice, s));
+      for (int l = 0; l < NLEV; l++) loff[l + 1] = loff[l] + hs[l];
+      std::vector<int> lo32(NLEV + 1);
+      for (int l = 0; l <= NLEV; l++) lo32[l] = (int)loff[l];
+      CUDA_OK(cudaMemcpyAsync(loffd, lo32.data(), 4 * (NLEV + 1), cudaMemcpyHostToDevice, s));
       k_scatter_levels<<<gpp, 256, (++c->launches, 0), s>>>(level, lrank, loffd, npts, llist);
       // the first batch: about first_batch points per instance
       const int fb = c->cfg.first_batch > 0 ? c->cfg.first_batch : 32;
       int64_t want = (int64_t)fb * ninst;
-      first_level = 32;
-      while (first_level > 0 && loff[33] - loff[first_level] < want) first_level--;
+      first_level = NLEV - 1;
+      while (first_level > 0 && loff[NLEV] - loff[first_level] < want) first_level--;
       if (getenv("GDT_NOBRIO")) first_level = 0;
       k_locate_init<D><<<gpp, 256, (++c->launches, 0), s>>>(T, npts, run.toff, run.inst_status, level, first_level,
                                                             act0, cnt);
@@ -1252,7 +1398,8 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       S.outer = (int*)pool_get(c, "eng.outer", 4 * (size_t)capCand * S.capB);
       S.count = cnt + 2;
       if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
-      CUDA_OK(cudaMemsetAsync(cnt + 1, 0, 16, s));
+      { int rcb = big_scratch(c, S, cnt); if (rcb) return rcb; }
+      CUDA_OK(cudaMemsetAsync(cnt + 1, 0, 20, s));
       CUDA_OK(cudaMemsetAsync(cnt + 8, 0, 4 * NBUCKET, s));
       unsigned gp = (unsigned)ceil_div(nact, 256);
       unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
@@ -1262,6 +1409,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
                                                         nullptr);
       ev[1] = mark();
       k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8, nullptr);
+      k_cavity_big<D><<<BIGCAP / 4, 128, (++c->launches, 0), s>>>(T, round, S, nullptr);
       ev[2] = mark();
       k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3, nullptr);
       ev[3] = mark();
@@ -1275,15 +1423,15 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
         if (ev[q] >= 0 && ev[q + 1] >= 0) recs.push_back({ev[q], ev[q + 1], q});
       if (getenv("GDT_DEBUG")) {
         int hc[5];
-        unsigned long long hd[6];
+        unsigned long long hd[7];
         cudaMemcpyAsync(hc, cnt, 20, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(hd, T.dbg, 48, cudaMemcpyDeviceToHost, s);
-        cudaMemsetAsync(T.dbg, 0, 48, s);
+        cudaMemcpyAsync(hd, T.dbg, 56, cudaMemcpyDeviceToHost, s);
+        cudaMemsetAsync(T.dbg, 0, 56, s);
         cudaStreamSynchronize(s);
         fprintf(stderr,
                 "round %u nact %d cand %d win %d walk %d steps %llu max %llu act_steps %llu act_max %llu "
-                "complete %llu grown %llu\n",
-                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3], hd[4], hd[5]);
+                "complete %llu grown %llu large %llu\n",
+                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3], hd[4], hd[5], hd[6]);
       }
       k_move_count<<<1, 1, (++c->launches, 0), s>>>(cnt + 0, cnt + 1);
       std::swap(ain, aout);

@@ -67,6 +67,13 @@ struct CandScratch {
   int* outer;     // capB entries per slot
   int* count;     // slots taken this round
   int cap, capC, capB;
+  // regions too large for the lists above (grown again by k_cavity_big)
+  int* bigcav;    // capCbig entries per large region
+  int* bigbnd;    // capBbig entries per large region
+  int* bigout;    // capBbig entries per large region
+  int* biglist;   // slot of each large region
+  int* nbig;      // large regions this round
+  int capCbig, capBbig;
 };
 
 // Host-side engine run: owns the buffers of one triangulation batch.

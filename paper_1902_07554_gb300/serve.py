@@ -66,6 +66,8 @@ class Server:
         self._queue: list[Job] = []            # arrived, not yet admitted (by arrival time)
         self._reserved = 0.0
         self._results: list[Result] = []
+        self._rows_out = 0                      # simplices copied back to the host
+        self._launches = 0                      # CUDA kernels launched by the library
         self._closed = False
         self._t0 = None
         self.peak_reserved = 0.0
@@ -148,8 +150,11 @@ class Server:
                     off[1:] = np.cumsum([len(j.points) for j in jobs])
                     outs, batched = tri.triangulate_batch(P, off), True
                 done = self.now()
+                launched = tri.stats().launches
                 with self._lock:
                     self._reserved -= need
+                    self._rows_out += sum(len(o) for o in outs)
+                    self._launches += launched
                     for j, o in zip(jobs, outs):
                         self._results.append(Result(j.jid, len(j.points), j.arrival, start, done,
                                                     o if self.keep else None, w, batched))
@@ -189,7 +194,8 @@ class Server:
                 "throughput_mpts": pts / span / 1e6 if span > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "batched_jobs": sum(r.batched for r in res),
-                "peak_reserved_gb": self.peak_reserved / 1e9}
+                "peak_reserved_gb": self.peak_reserved / 1e9, "rows_out": self._rows_out,
+                "launches": self._launches}
 
 
 def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:

@@ -125,3 +125,17 @@ def test_errors(tri):
     # the context stays usable after errors
     P = pointsets.uniform(500, 2, 9)
     assert np.array_equal(tri.triangulate(P).astype(np.int64), oracle.delaunay(P))
+
+
+@pytest.mark.parametrize("D,k", [(2, 1), (2, 4), (3, 1), (3, 8)])
+def test_large_region_path_matches_oracle(tri, D, k):
+    """Tiny regular region lists (cavity_cap = 8) send most regions through the
+    large-region pass (grown again with the pass bit in their key); the
+    result must still be the oracle's DT."""
+    P = pointsets.clustered(20_000, 9) if D == 3 else pointsets.normal(20_000, 2, 9)
+    tri.configure(cavity_cap=8, base_threshold=256)
+    try:
+        got = tri.triangulate(P, k=k, sample_frac=0.01).astype(np.int64)
+    finally:
+        tri.configure(cavity_cap=0, base_threshold=2048)
+    assert np.array_equal(got, oracle.delaunay(P))
