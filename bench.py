@@ -371,6 +371,22 @@ def main():
     value = job_value(n, world, ms_max)
     stats = tri.stats().as_dict()
 
+    # ---------------- the plain path: the same points, same engine, k = 1 (no divide)
+    plain_ms = []
+    for _ in range(max(args.steps, 3)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tri.triangulate(P_dev, k=1, sample_frac=w["frac"], fetch=False)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+    plain_step = max_over_ranks(sum(plain_ms) / len(plain_ms), dist, f"cuda:{local}")
+    plain = {"value": job_value(n, world, plain_step), "unit": "Mpoints/s", "ms_per_step": plain_step,
+             "what": "dt_triangulate with k = 1: the same insertion engine on all points, no divide, "
+                     "no border triangulation, no merge"}
+
     # ---------------- per-kernel times: the same K steps again with CUDA events
     # around every engine launch (kept out of the timed region: the events
     # themselves cost host time in the short rounds)
@@ -447,7 +463,7 @@ def main():
                    "rounds": "host-driven (profile mode)" if args.host_rounds else "one CUDA graph per engine run",
                    "l2": "flushed before every step (256 MiB write); working set > L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "e2e": e2e, "plain_path": plain, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": int(launches),
         "stats": {k: stats[k] for k in ("simplices", "eta", "border_vertices", "border_simplices", "imbalance",
                                          "cv", "o_dt", "rounds_max", "exact_calls", "ms_phase")},

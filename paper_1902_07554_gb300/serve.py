@@ -203,8 +203,12 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
 
 
-def k_for(n: int) -> int:
-    """Partitions for a job of n points: about 64k points per partition."""
-    if n < 131_072:
+def k_for(n: int, divide: bool = False) -> int:
+    """Partitions for a job of n points.  On one GPU the direct insertion
+    (k = 1) was faster than the divide-and-conquer path at every size measured
+    (1k to 4M points: the border triangulation and the sample DT cost more
+    than the smaller partial triangulations save), so jobs run directly unless
+    `divide` asks for about 64k points per partition."""
+    if not divide or n < 131_072:
         return 1
     return int(min(64, max(2, 2 ** round(math.log2(n / 65_536)))))

@@ -19,7 +19,7 @@ def _jobs(count, seed, lo, hi, rate):
     jobs = []
     for i in range(count):
         P = pointsets.job_points(sizes[i], kinds[i], seeds[i])
-        jobs.append(Job(float(arr[i]), i, P, k=k_for(len(P)), frac=0.005))
+        jobs.append(Job(float(arr[i]), i, P, k=k_for(len(P), divide=True), frac=0.005))
     return jobs
 
 
