@@ -345,20 +345,25 @@ __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, 
 // step.  Conflicting neighbours join the region (claimC/claimA atomicMax; the
 // returned old value also deduplicates lanes that reach the same simplex),
 // the others become boundary facets (ring claim in claimA).
-// One warp grows nominee p's conflict region into C (region simplices; NB:
-// optional copies of their links) and B (boundary facets), claiming as it
-// goes.  status: CAND_OK, CAND_LOST (met a stronger claim) or CAND_OVER (the
-// lists are full).
-template <int D>
-__device__ __forceinline__ void grow_region(const TriView<D>& T, int p, unsigned long long key, int* C, int4* NB, int* B,
-                                            int capC, int capB, int& nc_out, int& nbd_out, int& status_out,
-                                            unsigned long long& pbytes, unsigned long long& ptests) {
+// A group of G lanes (G = 32: a whole warp) grows nominee p's conflict region
+// into C (region simplices; NB: optional copies of their links) and B
+// (boundary facets), claiming as it goes; each step inspects G/(D+1) region
+// simplices x (D+1) facets.  Groups of one warp run side by side (warp-wide
+// ballots, each group reading its own bits).  has = false: an idle group.
+// status: CAND_OK, CAND_LOST (met a stronger claim) or CAND_OVER (lists full).
+template <int D, int G>
+__device__ __forceinline__ void grow_region(const TriView<D>& T, bool has, int p, unsigned long long key, int* C,
+                                            int4* NB, int* B, int capC, int capB, int& nc_out, int& nbd_out,
+                                            int& status_out, unsigned long long& pbytes, unsigned long long& ptests) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  constexpr int PER = 32 / (D + 1);
-  int t0 = T.loc[p];
-  int status = CAND_OK;
-  if (lane == 0) {
+  const int gl = lane % G, gbase = lane - gl;
+  const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << gbase);
+  const unsigned below = gmask & ((1u << lane) - 1u);
+  constexpr int PER = G / (D + 1);
+  int status = has ? CAND_OK : CAND_LOST;
+  int t0 = has ? T.loc[p] : 0;
+  if (has && gl == 0) {
     if (NB) NB[0] = T.tn[t0];
     // the located simplex carries p's pick (= key) already, except on a second
     // pass (key has its pass bit): claim it in both words so that no lane adds
@@ -369,13 +374,15 @@ __device__ __forceinline__ void grow_region(const TriView<D>& T, int p, unsigned
     C[0] = t0;
     pbytes += sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1) + 16 + 4;
   }
-  status = __shfl_sync(FULL, status, 0);
-  int nc = 1, nbd = 0;
+  status = __shfl_sync(FULL, status, gbase);
+  int nc = 1, nbd = 0, h = 0;
   __syncwarp();
-  for (int h = 0; h < nc && status == CAND_OK;) {
+  for (;;) {
+    const bool act = status == CAND_OK && h < nc;
+    if (!__any_sync(FULL, act)) break;
     const int nc0 = nc;                                // region simplices known at this step
-    int j = h + lane / (D + 1), i = lane % (D + 1);
-    bool valid = lane < PER * (D + 1) && j < nc0;
+    int j = h + gl / (D + 1), i = gl % (D + 1);
+    bool valid = act && gl < PER * (D + 1) && j < nc0;
     bool addC = false, addB = false, lost = false, bad = false;
     int t = -1, u = -1;
     int4 links = make_int4(0, 0, 0, 0);
@@ -419,19 +426,25 @@ __device__ __forceinline__ void grow_region(const TriView<D>& T, int p, unsigned
       }
     }
     if (bad) set_error(T.st, DT_E_INTERNAL, 10);
-    if (__any_sync(FULL, lost || bad)) { status = CAND_LOST; break; }
-    unsigned mC = __ballot_sync(FULL, addC), mB = __ballot_sync(FULL, addB);
-    int nC = __popc(mC), nB = __popc(mB);
-    if (nc + nC > capC || nbd + nB > capB) { status = CAND_OVER; break; }
-    unsigned lt = (1u << lane) - 1;
-    if (addC) {
-      C[nc + __popc(mC & lt)] = u;
-      if (NB) NB[nc + __popc(mC & lt)] = links;
+    const unsigned mL = __ballot_sync(FULL, lost || bad) & gmask;
+    const unsigned mC = __ballot_sync(FULL, addC) & gmask, mB = __ballot_sync(FULL, addB) & gmask;
+    if (act) {
+      const int nC = __popc(mC), nB = __popc(mB);
+      if (mL) {
+        status = CAND_LOST;
+      } else if (nc + nC > capC || nbd + nB > capB) {
+        status = CAND_OVER;
+      } else {
+        if (addC) {
+          C[nc + __popc(mC & below)] = u;
+          if (NB) NB[nc + __popc(mC & below)] = links;
+        }
+        if (addB) B[nbd + __popc(mB & below)] = pack_nb(t, i);
+        nc += nC;
+        nbd += nB;
+        h = min(h + PER, nc0);                         // simplices appended now come next
+      }
     }
-    if (addB) B[nbd + __popc(mB & lt)] = pack_nb(t, i);
-    nc += nC;
-    nbd += nB;
-    h = min(h + PER, nc0);                             // simplices appended now come next
     __syncwarp();
   }
   nc_out = nc;
@@ -439,57 +452,65 @@ __device__ __forceinline__ void grow_region(const TriView<D>& T, int p, unsigned
   status_out = status;
 }
 
-template <int D>
-__device__ __forceinline__ void region_stats(const TriView<D>& T, int status, int nc, unsigned long long pbytes,
-                                             unsigned long long ptests) {
+// Profile and debug counters of a group's region (group leader).
+template <int D, int G>
+__device__ __forceinline__ void region_stats(const TriView<D>& T, bool has, int status, int nc,
+                                             unsigned long long pbytes, unsigned long long ptests) {
   const unsigned FULL = 0xffffffffu;
   if (T.prof) {
     for (int off = 16; off; off >>= 1) {
       pbytes += __shfl_down_sync(FULL, pbytes, off);
       ptests += __shfl_down_sync(FULL, ptests, off);
     }
+    if ((threadIdx.x & 31) == 0) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (T.dbg) {   // [4] complete regions, [5] region simplices grown by all nominees, [6] large regions
-      if (status == CAND_OK) atomicAdd(&T.dbg[4], 1ull);
-      atomicAdd(&T.dbg[5], (unsigned long long)nc);
-    }
-    if (T.prof) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
+  if (T.dbg && has && (threadIdx.x & 31) % G == 0) {
+    // [4] complete regions, [5] region simplices grown by all nominees
+    if (status == CAND_OK) atomicAdd(&T.dbg[4], 1ull);
+    atomicAdd(&T.dbg[5], (unsigned long long)nc);
   }
 }
 
-// One warp per nominee, strongest list first.  A region that outgrows the
-// regular lists is queued for k_cavity_big (up to BIGCAP per round).
+// Nominees in groups of CAV_G lanes (32 / CAV_G per warp), strongest list
+// first.  A region that outgrows the regular lists is queued for
+// k_cavity_big (up to BIGCAP per round).
+constexpr int CAV_G = 32;
+
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
                                                   CandScratch S, const int* bcnt, const EngCtl* ctl) {
   pdl_enter();
   if (ctl) round = ctl->round;
-  int lane = threadIdx.x & 31;
-  int nwarp = (gridDim.x * blockDim.x) >> 5;
-  int nnom = min(*nnom_p, S.cap);
+  constexpr int GPW = 32 / CAV_G;                      // groups per warp
+  const int lane = threadIdx.x & 31, grp = lane / CAV_G, gl = lane % CAV_G;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int nnom = min(*nnom_p, S.cap);
   // the region list lives in shared memory while it fits (copied out at the end)
   // together with the neighbour links of each region simplex (loaded when the
   // simplex joins, beside its claims, instead of one step later)
   constexpr int SHC = 128;
-  __shared__ int s_region[4][SHC];
-  __shared__ int4 s_links[4][SHC];
+  __shared__ int s_region[4 * GPW][SHC];
+  __shared__ int4 s_links[4 * GPW][SHC];
   const bool in_shared = S.capC <= SHC && blockDim.x <= 128;
-  for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < nnom; slot += nwarp) {
-    int p = nominee_at(nom, bcnt, S.cap, slot);
-    unsigned long long key = mkkey(round, p);
-    int* Cg = S.cav + (int64_t)slot * S.capC;
-    int* C = in_shared ? s_region[threadIdx.x >> 5] : Cg;
-    int4* NB = in_shared ? s_links[threadIdx.x >> 5] : nullptr;
-    int* B = S.bnd + (int64_t)slot * S.capB;
-    if (lane == 0) S.cand[slot] = p;
+  const int sg = (threadIdx.x >> 5) * GPW + grp;
+  for (int first = wid * GPW; first < nnom; first += nwarp * GPW) {
+    const int slot = first + grp;
+    const bool has = slot < nnom;
+    const int p = has ? nominee_at(nom, bcnt, S.cap, slot) : 0;
+    const unsigned long long key = mkkey(round, p);
+    int* Cg = S.cav + (int64_t)(has ? slot : 0) * S.capC;
+    int* C = in_shared ? s_region[sg] : Cg;
+    int4* NB = in_shared ? s_links[sg] : nullptr;
+    int* B = S.bnd + (int64_t)(has ? slot : 0) * S.capB;
+    if (has && gl == 0) S.cand[slot] = p;
     unsigned long long pbytes = 0, ptests = 0;
     int nc, nbd, status;
-    grow_region<D>(T, p, key, C, NB, B, S.capC, S.capB, nc, nbd, status, pbytes, ptests);
-    if (in_shared && status == CAND_OK)
-      for (int q = lane; q < nc; q += 32) Cg[q] = C[q];
-    region_stats<D>(T, status, nc, pbytes, ptests);
-    if (lane == 0) {
+    grow_region<D, CAV_G>(T, has, p, key, C, NB, B, S.capC, S.capB, nc, nbd, status, pbytes, ptests);
+    if (has && in_shared && status == CAND_OK)
+      for (int q = gl; q < nc; q += CAV_G) Cg[q] = C[q];
+    region_stats<D, CAV_G>(T, has, status, nc, pbytes, ptests);
+    if (has && gl == 0) {
       if (status == CAND_OVER) {
         if (T.dbg) atomicAdd(&T.dbg[6], 1ull);
         const int q = atomicAdd(S.nbig, 1);
@@ -520,8 +541,8 @@ __global__ void __launch_bounds__(128) k_cavity_big(TriView<D> T, unsigned round
     int* B = S.bigbnd + (int64_t)q * S.capBbig;
     unsigned long long pbytes = 0, ptests = 0;
     int nc, nbd, status;
-    grow_region<D>(T, p, key, C, nullptr, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
-    region_stats<D>(T, status, nc, pbytes, ptests);
+    grow_region<D, 32>(T, true, p, key, C, nullptr, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
+    region_stats<D, 32>(T, true, status, nc, pbytes, ptests);
     if (lane == 0) {
       if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
       S.meta[slot] = make_int4(nc, nbd, status, q + 1);
@@ -625,15 +646,28 @@ __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, 
     }
     __syncwarp();
     // phase 3: retire the region.  A dead slot redirects to a new simplex
-    // that lies on one of its own boundary facets when it has one (the
-    // points it held are then a step or two away), else to the first one.
-    for (int h = lane; h < nc; h += 32) {
-      int t = C[h];
-      *comp_ptr(T.tv, t, 0) = DEAD;
-      *comp_ptr(T.tn, t, 0) = pack_nb(base, 0);
-    }
-    __syncwarp();
+    // near the points it held: the one over one of its own boundary facets,
+    // else the one a neighbouring region simplex redirects to, else the
+    // first one.  (Until now every link of a region simplex is an old slot,
+    // below every base of this round, so a link into [base, base + nbd) is
+    // a redirect already written.)
+    for (int h = lane; h < nc; h += 32) *comp_ptr(T.tv, C[h], 0) = DEAD;
     for (int b = lane; b < nbd; b += 32) *comp_ptr(T.tn, nb_simplex(B[b]), 0) = pack_nb(base + b, 0);
+    __syncwarp();
+    for (int h = lane; h < nc; h += 32) {
+      const int t = C[h];
+      const int4 nt = T.tn[t];
+      auto fresh = [&](int link) { const int q = nb_simplex(link); return link >= 0 && q >= base && q < base + nbd; };
+      if (fresh(nt.x)) continue;
+      int red = pack_nb(base, 0);
+      for (int k = 0; k <= D; k++) {
+        const int u = nb_simplex(get4(nt, k));
+        if (!slot_ok(T, u)) continue;
+        const int r = *comp_ptr(T.tn, u, 0);
+        if (fresh(r)) { red = r; break; }
+      }
+      *comp_ptr(T.tn, t, 0) = red;
+    }
     if (lane == 0) {
       T.state[p] = 1;
       T.loc[p] = base;
