@@ -91,7 +91,11 @@ typedef struct dt_config {
   int first_batch;       /* points per instance in the first insertion batch (BRIO); 0 = automatic (32) */
   int brio_growth;       /* BRIO batch growth x 100: each batch has about (growth - 1) times the points
                             inserted before it; 0 = automatic (150) */
-  int reserved[4];
+  int small_rounds;      /* rounds with at most this many active points run inside one thread block
+                            (no launches between their phases); 0 or -1 = never (the default: on
+                            GB300 the per-round latency is the phases' memory chains, not the
+                            launches, so the graph of separate kernels is as fast or faster) */
+  int reserved[3];
 } dt_config;
 
 typedef struct dt_stats {

@@ -123,6 +123,8 @@ struct EngCtl {
   int stalled;         // consecutive rounds without an insertion
   int activated;       // points activated this round
   int done;            // 0 running; 1 finished; 2 device error; 3 stalled; 4 round limit
+  int small;           // 1: the next rounds are small enough for k_small_rounds (one CTA)
+  int small_max;       // active points up to which a round counts as small
 };
 
 // Programmatic dependent launch inside the round graph: each round kernel
@@ -289,7 +291,10 @@ __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, 
                                                   int* nom, int* nnom, int* bcnt, int seg, const EngCtl* ctl) {
   pdl_enter();
   __shared__ int s_cnt[NBUCKET], s_base[NBUCKET];
-  if (ctl) { act = ctl->ain; round = ctl->round; }
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    act = ctl->ain; round = ctl->round;
+  }
   const int nact = *nact_p;
   for (int64_t blk = (int64_t)blockIdx.x * blockDim.x; blk < nact; blk += (int64_t)gridDim.x * blockDim.x) {
   __syncthreads();
@@ -480,7 +485,10 @@ template <int D>
 __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
                                                   CandScratch S, const int* bcnt, const EngCtl* ctl) {
   pdl_enter();
-  if (ctl) round = ctl->round;
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    round = ctl->round;
+  }
   constexpr int GPW = 32 / CAV_G;                      // groups per warp
   const int lane = threadIdx.x & 31, grp = lane / CAV_G, gl = lane % CAV_G;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -523,159 +531,178 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
   }
 }
 
+// Second growth of large region q (one warp).
+template <int D>
+__device__ __forceinline__ void big_region(const TriView<D>& T, unsigned round, const CandScratch& S, int q) {
+  const int lane = threadIdx.x & 31;
+  const int slot = S.biglist[q];
+  const int p = S.cand[slot];
+  const unsigned long long key = mkkey(round, p) | 1ull;   // second pass: see mkkey
+  int* C = S.bigcav + (int64_t)q * S.capCbig;
+  int* B = S.bigbnd + (int64_t)q * S.capBbig;
+  unsigned long long pbytes = 0, ptests = 0;
+  int nc, nbd, status;
+  grow_region<D, 32>(T, true, p, key, C, nullptr, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
+  region_stats<D, 32>(T, true, status, nc, pbytes, ptests);
+  if (lane == 0) {
+    if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
+    S.meta[slot] = make_int4(nc, nbd, status, q + 1);
+  }
+  __syncwarp();
+}
+
 // Large regions: the nominees whose region outgrew the regular lists grow it
 // again into lists of capCbig / capBbig entries (their claims so far stand;
 // atomicMax makes the repeated claims harmless).
 template <int D>
 __global__ void __launch_bounds__(128) k_cavity_big(TriView<D> T, unsigned round, CandScratch S, const EngCtl* ctl) {
   pdl_enter();
-  if (ctl) round = ctl->round;
-  const int lane = threadIdx.x & 31;
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    round = ctl->round;
+  }
   const int nwarp = (gridDim.x * blockDim.x) >> 5;
   const int nbig = min(*S.nbig, BIGCAP);
-  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nbig; q += nwarp) {
-    const int slot = S.biglist[q];
-    const int p = S.cand[slot];
-    const unsigned long long key = mkkey(round, p) | 1ull;   // second pass: see mkkey
-    int* C = S.bigcav + (int64_t)q * S.capCbig;
-    int* B = S.bigbnd + (int64_t)q * S.capBbig;
-    unsigned long long pbytes = 0, ptests = 0;
-    int nc, nbd, status;
-    grow_region<D, 32>(T, true, p, key, C, nullptr, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
-    region_stats<D, 32>(T, true, status, nc, pbytes, ptests);
-    if (lane == 0) {
-      if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
-      S.meta[slot] = make_int4(nc, nbd, status, q + 1);
-    }
-    __syncwarp();
-  }
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nbig; q += nwarp) big_region<D>(T, round, S, q);
 }
 
 // One warp per nominee: a nominee wins if no stronger nominee claimed any of
 // its region (claimA) or has any of its ring in its own region (claimC).
 // Winners replace their region by the star of new simplices in fresh slots.
+// Insertion of the candidate in `slot` if it won (one warp): verify the
+// claims, build the star over the boundary, retire the region.
+template <int D>
+__device__ __forceinline__ void insert_winner(const TriView<D>& T, unsigned round, const CandScratch& S, int slot,
+                                              int* nwin) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+
+  int4 m = S.meta[slot];
+  if (m.z != CAND_OK) return;
+  int p = S.cand[slot];
+  const bool big = m.w > 0;
+  const unsigned long long key = mkkey(round, p) | (big ? 1ull : 0ull);
+  const int* C = big ? S.bigcav + (int64_t)(m.w - 1) * S.capCbig : S.cav + (int64_t)slot * S.capC;
+  const int* B = big ? S.bigbnd + (int64_t)(m.w - 1) * S.capBbig : S.bnd + (int64_t)slot * S.capB;
+  int* OUT = big ? S.bigout + (int64_t)(m.w - 1) * S.capBbig : S.outer + (int64_t)slot * S.capB;
+  int nc = m.x, nbd = m.y;
+  bool ok = true;
+  for (int j = lane; j < nc; j += 32)
+    if (*((volatile unsigned long long*)&T.claimA[C[j]]) != key) ok = false;
+  // a region shared with a stronger winner may already carry its tags: stop here
+  if (!__all_sync(FULL, ok)) return;
+  for (int b = lane; b < nbd; b += 32) {
+    int t = nb_simplex(B[b]), i = nb_face(B[b]);
+    int u = nb_simplex(*comp_ptr(T.tn, t, i));
+    if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 12); ok = false; }
+    else if (*((volatile unsigned long long*)&T.claimC[u]) > key) ok = false;
+  }
+  if (!__all_sync(FULL, ok)) return;
+  int inst = T.pinst[p];
+  int base = 0;
+  if (lane == 0) base = atomicAdd(&T.tcount[inst], nbd);
+  base = __shfl_sync(FULL, base, 0);
+  if (base + nbd > T.tend[inst]) {
+    if (lane == 0) set_error(T.st, DT_E_OVERFLOW, 1);
+    return;
+  }
+  // phase 1: remember the outside links, tag boundary facets with their new simplex
+  for (int b = lane; b < nbd; b += 32) {
+    int t = nb_simplex(B[b]), i = nb_face(B[b]);
+    int* cp = comp_ptr(T.tn, t, i);
+    OUT[b] = *cp;
+    *cp = TAGBIT | (base + b);
+  }
+  __syncwarp();
+  // phase 2: build the star of p over the boundary
+  for (int b = lane; b < nbd; b += 32) {
+    int t = nb_simplex(B[b]), i = nb_face(B[b]);
+    int4 vv = T.tv[t];
+    set4(vv, i, p);
+    int4 nn = make_int4(0, 0, 0, 0);
+    int out = OUT[b];
+    set4(nn, i, out);
+    if (slot_ok(T, nb_simplex(out))) *comp_ptr(T.tn, nb_simplex(out), nb_face(out)) = pack_nb(base + b, i);
+    else set_error(T.st, DT_E_INTERNAL, 13);
+    for (int j = 0; j <= D; j++) {
+      if (j == i) continue;
+      // rotate around the ridge (t minus slots i and j) inside the region
+      int cur = t, as = j, bs = i;
+      int link = -1;
+      for (int it = 0; it <= nc + 1; it++) {
+        int nx = *comp_ptr(T.tn, cur, as);
+        if (nx < 0) { link = pack_nb(nx & ~TAGBIT, bs); break; }
+        int nxt = nb_simplex(nx);
+        if (!slot_ok(T, nxt)) break;
+        int bvtx = get4(T.tv[cur], bs);
+        int4 nv = T.tv[nxt];
+        int nas = -1;
+        for (int l = 0; l <= D; l++) if (get4(nv, l) == bvtx) nas = l;
+        bs = nb_face(nx);
+        as = nas;
+        cur = nxt;
+        if (as < 0) break;
+      }
+      if (link < 0) {
+        if (atomicCAS(&T.st->error, 0, DT_E_INTERNAL) == 0) {
+          T.st->detail = 2;
+          int* d = T.st->dbg;
+          d[0] = (int)round; d[1] = p; d[2] = nc; d[3] = nbd; d[4] = b; d[5] = j; d[6] = t; d[7] = i;
+          d[8] = cur; d[9] = as; d[10] = bs; d[11] = slot;
+        }
+        link = 0;
+      }
+      set4(nn, j, link);
+    }
+    T.tv[base + b] = vv;
+    T.tn[base + b] = nn;
+  }
+  __syncwarp();
+  // phase 3: retire the region.  A dead slot redirects to a new simplex
+  // near the points it held: the one over one of its own boundary facets,
+  // else the one a neighbouring region simplex redirects to, else the
+  // first one.  (Until now every link of a region simplex is an old slot,
+  // below every base of this round, so a link into [base, base + nbd) is
+  // a redirect already written.)
+  for (int h = lane; h < nc; h += 32) *comp_ptr(T.tv, C[h], 0) = DEAD;
+  for (int b = lane; b < nbd; b += 32) *comp_ptr(T.tn, nb_simplex(B[b]), 0) = pack_nb(base + b, 0);
+  __syncwarp();
+  for (int h = lane; h < nc; h += 32) {
+    const int t = C[h];
+    const int4 nt = T.tn[t];
+    auto fresh = [&](int link) { const int q = nb_simplex(link); return link >= 0 && q >= base && q < base + nbd; };
+    if (fresh(nt.x)) continue;
+    int red = pack_nb(base, 0);
+    for (int k = 0; k <= D; k++) {
+      const int u = nb_simplex(get4(nt, k));
+      if (!slot_ok(T, u)) continue;
+      const int r = *comp_ptr(T.tn, u, 0);
+      if (fresh(r)) { red = r; break; }
+    }
+    *comp_ptr(T.tn, t, 0) = red;
+  }
+  if (lane == 0) {
+    T.state[p] = 1;
+    T.loc[p] = base;
+    atomicAdd(nwin, 1);
+    if (T.hint) T.hint[hint_cell(T, p)] = base;
+  }
+  __syncwarp();
+
+}
+
 template <int D>
 __global__ void __launch_bounds__(128) k_insert_w(TriView<D> T, unsigned round, CandScratch S, const int* nnom_p,
                                                   int* nwin, const EngCtl* ctl) {
   pdl_enter();
-  const unsigned FULL = 0xffffffffu;
-  if (ctl) round = ctl->round;
-  int lane = threadIdx.x & 31;
-  int nwarp = (gridDim.x * blockDim.x) >> 5;
-  int total = min(*nnom_p, S.cap);
-  for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nwarp) {
-    int4 m = S.meta[slot];
-    if (m.z != CAND_OK) continue;
-    int p = S.cand[slot];
-    const bool big = m.w > 0;
-    const unsigned long long key = mkkey(round, p) | (big ? 1ull : 0ull);
-    const int* C = big ? S.bigcav + (int64_t)(m.w - 1) * S.capCbig : S.cav + (int64_t)slot * S.capC;
-    const int* B = big ? S.bigbnd + (int64_t)(m.w - 1) * S.capBbig : S.bnd + (int64_t)slot * S.capB;
-    int* OUT = big ? S.bigout + (int64_t)(m.w - 1) * S.capBbig : S.outer + (int64_t)slot * S.capB;
-    int nc = m.x, nbd = m.y;
-    bool ok = true;
-    for (int j = lane; j < nc; j += 32)
-      if (*((volatile unsigned long long*)&T.claimA[C[j]]) != key) ok = false;
-    // a region shared with a stronger winner may already carry its tags: stop here
-    if (!__all_sync(FULL, ok)) continue;
-    for (int b = lane; b < nbd; b += 32) {
-      int t = nb_simplex(B[b]), i = nb_face(B[b]);
-      int u = nb_simplex(*comp_ptr(T.tn, t, i));
-      if (!slot_ok(T, u)) { set_error(T.st, DT_E_INTERNAL, 12); ok = false; }
-      else if (*((volatile unsigned long long*)&T.claimC[u]) > key) ok = false;
-    }
-    if (!__all_sync(FULL, ok)) continue;
-    int inst = T.pinst[p];
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&T.tcount[inst], nbd);
-    base = __shfl_sync(FULL, base, 0);
-    if (base + nbd > T.tend[inst]) {
-      if (lane == 0) set_error(T.st, DT_E_OVERFLOW, 1);
-      continue;
-    }
-    // phase 1: remember the outside links, tag boundary facets with their new simplex
-    for (int b = lane; b < nbd; b += 32) {
-      int t = nb_simplex(B[b]), i = nb_face(B[b]);
-      int* cp = comp_ptr(T.tn, t, i);
-      OUT[b] = *cp;
-      *cp = TAGBIT | (base + b);
-    }
-    __syncwarp();
-    // phase 2: build the star of p over the boundary
-    for (int b = lane; b < nbd; b += 32) {
-      int t = nb_simplex(B[b]), i = nb_face(B[b]);
-      int4 vv = T.tv[t];
-      set4(vv, i, p);
-      int4 nn = make_int4(0, 0, 0, 0);
-      int out = OUT[b];
-      set4(nn, i, out);
-      if (slot_ok(T, nb_simplex(out))) *comp_ptr(T.tn, nb_simplex(out), nb_face(out)) = pack_nb(base + b, i);
-      else set_error(T.st, DT_E_INTERNAL, 13);
-      for (int j = 0; j <= D; j++) {
-        if (j == i) continue;
-        // rotate around the ridge (t minus slots i and j) inside the region
-        int cur = t, as = j, bs = i;
-        int link = -1;
-        for (int it = 0; it <= nc + 1; it++) {
-          int nx = *comp_ptr(T.tn, cur, as);
-          if (nx < 0) { link = pack_nb(nx & ~TAGBIT, bs); break; }
-          int nxt = nb_simplex(nx);
-          if (!slot_ok(T, nxt)) break;
-          int bvtx = get4(T.tv[cur], bs);
-          int4 nv = T.tv[nxt];
-          int nas = -1;
-          for (int l = 0; l <= D; l++) if (get4(nv, l) == bvtx) nas = l;
-          bs = nb_face(nx);
-          as = nas;
-          cur = nxt;
-          if (as < 0) break;
-        }
-        if (link < 0) {
-          if (atomicCAS(&T.st->error, 0, DT_E_INTERNAL) == 0) {
-            T.st->detail = 2;
-            int* d = T.st->dbg;
-            d[0] = (int)round; d[1] = p; d[2] = nc; d[3] = nbd; d[4] = b; d[5] = j; d[6] = t; d[7] = i;
-            d[8] = cur; d[9] = as; d[10] = bs; d[11] = slot;
-          }
-          link = 0;
-        }
-        set4(nn, j, link);
-      }
-      T.tv[base + b] = vv;
-      T.tn[base + b] = nn;
-    }
-    __syncwarp();
-    // phase 3: retire the region.  A dead slot redirects to a new simplex
-    // near the points it held: the one over one of its own boundary facets,
-    // else the one a neighbouring region simplex redirects to, else the
-    // first one.  (Until now every link of a region simplex is an old slot,
-    // below every base of this round, so a link into [base, base + nbd) is
-    // a redirect already written.)
-    for (int h = lane; h < nc; h += 32) *comp_ptr(T.tv, C[h], 0) = DEAD;
-    for (int b = lane; b < nbd; b += 32) *comp_ptr(T.tn, nb_simplex(B[b]), 0) = pack_nb(base + b, 0);
-    __syncwarp();
-    for (int h = lane; h < nc; h += 32) {
-      const int t = C[h];
-      const int4 nt = T.tn[t];
-      auto fresh = [&](int link) { const int q = nb_simplex(link); return link >= 0 && q >= base && q < base + nbd; };
-      if (fresh(nt.x)) continue;
-      int red = pack_nb(base, 0);
-      for (int k = 0; k <= D; k++) {
-        const int u = nb_simplex(get4(nt, k));
-        if (!slot_ok(T, u)) continue;
-        const int r = *comp_ptr(T.tn, u, 0);
-        if (fresh(r)) { red = r; break; }
-      }
-      *comp_ptr(T.tn, t, 0) = red;
-    }
-    if (lane == 0) {
-      T.state[p] = 1;
-      T.loc[p] = base;
-      atomicAdd(nwin, 1);
-      if (T.hint) T.hint[hint_cell(T, p)] = base;
-    }
-    __syncwarp();
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    round = ctl->round;
   }
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int total = min(*nnom_p, S.cap);
+  for (int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nwarp)
+    insert_winner<D>(T, round, S, slot, nwin);
 }
 
 // Visibility walk to a simplex in conflict with point p: a finite simplex
@@ -721,74 +748,96 @@ __device__ int walk_to(const TriView<D>& T, int s, int p, int limit, int* steps_
 
 // Keeps uninserted points for the next round; points whose simplex died go
 // to the walker list, the others make the next round's pick right away.
+// Relocation check of the 32 active points from `base` (one warp): points
+// still uninserted stay active; those whose simplex died go to the walk list,
+// the others pick their simplex for the next round.
+template <int D>
+__device__ __forceinline__ void reloc_check_warp(const TriView<D>& T, const int* act, int nact, int* act_out,
+                                                 int* nact_out, int* walk, int* nwalk, unsigned next_round,
+                                                 int64_t base) {
+  const int64_t idx = base + (threadIdx.x & 31);
+  bool keep = false, walker = false;
+  int p = -1;
+  if (idx < nact) {
+    p = act[idx];
+    if (T.state[p] == 0) {
+      keep = true;
+      int s = T.loc[p];
+      if (*comp_ptr(T.tv, s, 0) == DEAD) walker = true;
+      else atomicMax(&T.claimC[s], mkkey(next_round, p));
+    }
+  }
+  warp_append(act_out, nact_out, keep, p);
+  warp_append(walk, nwalk, walker, p);
+  if (T.prof) {
+    // act 4, state 1, loc 4, slot word 4, pick 8, output 4
+    unsigned long long b = idx < nact ? 25 : 0;
+    for (int off = 16; off; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[3], b);
+  }
+}
+
 template <int D>
 __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, int* act_out, int* nact_out,
                               int* walk, int* nwalk, unsigned next_round, const EngCtl* ctl) {
   pdl_enter();
-  if (ctl) { act = ctl->ain; act_out = ctl->aout; next_round = ctl->round + 1; }
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    act = ctl->ain; act_out = ctl->aout; next_round = ctl->round + 1;
+  }
   const int nact = *nact_p;
   // warp-uniform grid-stride loop (warp_append needs every lane)
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < nact;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t idx = base + (threadIdx.x & 31);
-    bool keep = false, walker = false;
-    int p = -1;
-    if (idx < nact) {
-      p = act[idx];
-      if (T.state[p] == 0) {
-        keep = true;
-        int s = T.loc[p];
-        if (*comp_ptr(T.tv, s, 0) == DEAD) walker = true;
-        else atomicMax(&T.claimC[s], mkkey(next_round, p));
-      }
-    }
-    warp_append(act_out, nact_out, keep, p);
-    warp_append(walk, nwalk, walker, p);
-    if (T.prof) {
-      // act 4, state 1, loc 4, slot word 4, pick 8, output 4
-      unsigned long long b = idx < nact ? 25 : 0;
-      for (int off = 16; off; off >>= 1) b += __shfl_down_sync(0xffffffffu, b, off);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&T.prof[3], b);
-    }
-  }
+       base += (int64_t)gridDim.x * blockDim.x)
+    reloc_check_warp<D>(T, act, nact, act_out, nact_out, walk, nwalk, next_round, base);
 }
 
 // Activates a batch of dormant points: from the simplex each was parked on,
 // follow the redirects of dead simplices to a live one, walk to a simplex in
 // conflict with the point, make its pick for the next round, and append it
 // to the active list.
+// Activation of the 32 dormant points from `base` of list (one warp):
+// locate each from its hint cell (or its parked simplex) and pick.
+template <int D>
+__device__ __forceinline__ void activate_warp(const TriView<D>& T, const int* list, int m, int* act, int* nact,
+                                              unsigned next_round, int64_t base) {
+  const int64_t idx = base + (threadIdx.x & 31);
+  bool ok = false;
+  int p = -1;
+  if (idx < m) {
+    p = list[idx];
+    int s = T.loc[p];
+    if (T.hint) {
+      int h = T.hint[hint_cell(T, p)];
+      if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
+    }
+    for (int hop = 0; hop < (1 << 16) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
+      s = nb_simplex(*comp_ptr(T.tn, s, 0));
+    int steps = 0;
+    int r = walk_to(T, s, p, 1 << 16, &steps);
+    if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
+    if (r < 0) {
+      set_error(T.st, DT_E_TIMEOUT, 4);
+    } else {
+      T.loc[p] = r;
+      atomicMax(&T.claimC[r], mkkey(next_round, p));
+      ok = true;
+    }
+  }
+  warp_append(act, nact, ok, p);
+}
+
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_activate(TriView<D> T, const int* list, int m, int* act, int* nact,
                                                   unsigned next_round, const EngCtl* ctl) {
   pdl_enter();
-  if (ctl) { list += ctl->act_lo; m = ctl->act_n; act = ctl->ain; next_round = ctl->round; }
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < m;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t idx = base + (threadIdx.x & 31);
-    bool ok = false;
-    int p = -1;
-    if (idx < m) {
-      p = list[idx];
-      int s = T.loc[p];
-      if (T.hint) {
-        int h = T.hint[hint_cell(T, p)];
-        if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
-      }
-      for (int hop = 0; hop < (1 << 20) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
-        s = nb_simplex(*comp_ptr(T.tn, s, 0));
-      int steps = 0;
-      int r = walk_to(T, s, p, 1 << 22, &steps);
-      if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
-      if (r < 0) {
-        set_error(T.st, DT_E_TIMEOUT, 4);
-      } else {
-        T.loc[p] = r;
-        atomicMax(&T.claimC[r], mkkey(next_round, p));
-        ok = true;
-      }
-    }
-    warp_append(act, nact, ok, p);
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    list += ctl->act_lo; m = ctl->act_n; act = ctl->ain; next_round = ctl->round;
   }
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < m;
+       base += (int64_t)gridDim.x * blockDim.x)
+    activate_warp<D>(T, list, m, act, nact, next_round, base);
 }
 
 // Opt-in self-check of the mesh (GDT_CHECK): every live simplex's links are
@@ -827,25 +876,32 @@ __global__ void k_check_mesh(TriView<D> T, const int* toff, const int* tcount, i
   }
 }
 
+// Relocation walk of point p whose simplex died.
+template <int D>
+__device__ __forceinline__ void reloc_walk_one(const TriView<D>& T, int p, unsigned next_round) {
+  int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
+  int steps = 0;
+  int r = walk_to(T, s, p, 1 << 16, &steps);
+  if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); return; }
+  T.loc[p] = r;
+  atomicMax(&T.claimC[r], mkkey(next_round, p));
+  // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
+  if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
+  if (T.dbg) { atomicAdd(&T.dbg[0], (unsigned long long)steps); atomicMax(&T.dbg[1], (unsigned long long)steps); }
+}
+
 template <int D>
 __global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* walk, const int* nwalk_p,
                                                     unsigned next_round, const EngCtl* ctl) {
   pdl_enter();
-  if (ctl) next_round = ctl->round + 1;
+  if (ctl) {
+    if (ctl->small || ctl->done) return;
+    next_round = ctl->round + 1;
+  }
   const int nwalk = *nwalk_p;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nwalk;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int p = walk[idx];
-    int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
-    int steps = 0;
-    int r = walk_to(T, s, p, 1 << 22, &steps);
-    if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); continue; }
-    T.loc[p] = r;
-    atomicMax(&T.claimC[r], mkkey(next_round, p));
-    // per step: vertex tuple 16, links 16, D+1 points; per point: 4 + 4 + 8
-    if (T.prof) atomicAdd(&T.prof[2], (unsigned long long)steps * (32 + (D + 1) * sizeof(typename PT<D>::T)) + 16);
-    if (T.dbg) { atomicAdd(&T.dbg[0], (unsigned long long)steps); atomicMax(&T.dbg[1], (unsigned long long)steps); }
-  }
+       idx += (int64_t)gridDim.x * blockDim.x)
+    reloc_walk_one<D>(T, walk[idx], next_round);
 }
 
 __device__ __forceinline__ unsigned long long ord_key(double x) {
@@ -894,6 +950,7 @@ __device__ void round_begin(EngCtl& C, int* cnt, const int* loffd) {
   C.act_lo = lo < 0 ? 0 : lo;
   C.act_n = lo < 0 ? 0 : hi - lo;
   C.activated = C.act_n;
+  C.small = nact <= C.small_max ? 1 : 0;
   if (nact > 0) C.round++;
   if (C.round > 400000 && C.done == 0) C.done = 4;
   cnt[1] = cnt[2] = cnt[3] = cnt[4] = cnt[5] = 0;
@@ -910,11 +967,7 @@ __global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
 // becomes current; the loop ends when nothing is left, on a device error,
 // after 4 rounds in a row without an insertion (a cavity overflowed its
 // scratch: the host grows it), or at the round limit.  One thread.
-__global__ void k_round_step(EngCtl* ctl, int* cnt, const int* loffd, const DevStatus* st,
-                             cudaGraphConditionalHandle handle) {
-  pdl_enter();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  EngCtl& C = *ctl;
+__device__ void round_end_begin(EngCtl& C, int* cnt, const int* loffd, const DevStatus* st) {
   const int had = cnt[0];
   const int nnew = cnt[1];
   cnt[0] = nnew;
@@ -930,7 +983,114 @@ __global__ void k_round_step(EngCtl* ctl, int* cnt, const int* loffd, const DevS
   }
   C.last_nact = nnew;
   if (C.done == 0) round_begin(C, cnt, loffd);
+}
+
+__global__ void k_round_step(EngCtl* ctl, int* cnt, const int* loffd, const DevStatus* st,
+                             cudaGraphConditionalHandle handle) {
+  pdl_enter();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  EngCtl& C = *ctl;
+  // small rounds were run and closed by k_small_rounds
+  if (!C.small) round_end_begin(C, cnt, loffd, st);
   cudaGraphSetConditional(handle, C.done == 0 ? 1u : 0u);
+}
+
+// Nomination of the 32 active points from `base` into one list (small rounds).
+template <int D>
+__device__ __forceinline__ void nominate_warp(const TriView<D>& T, const int* act, int nact, unsigned round,
+                                              int* nom, int* nnom, int64_t base) {
+  const int64_t idx = base + (threadIdx.x & 31);
+  bool take = false;
+  int p = -1;
+  if (idx < nact) {
+    p = act[idx];
+    const unsigned long long key = mkkey(round, p);
+    const int t0 = T.loc[p];
+    if (*((volatile unsigned long long*)&T.claimC[t0]) == key) {
+      take = true;
+      const int4 nn0 = T.tn[t0];
+      for (int i = 0; i <= D; i++) {
+        const int u = nb_simplex(get4(nn0, i));
+        if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) take = false;
+      }
+    }
+  }
+  warp_append(nom, nnom, take, p);
+}
+
+// Region growth of the nominee in `slot` with its lists in global memory (one warp).
+template <int D>
+__device__ __forceinline__ void cavity_slot(const TriView<D>& T, unsigned round, const CandScratch& S, const int* nom,
+                                            const int* bcnt, int slot) {
+  const int lane = threadIdx.x & 31;
+  const int p = nominee_at(nom, bcnt, S.cap, slot);
+  const unsigned long long key = mkkey(round, p);
+  int* C = S.cav + (int64_t)slot * S.capC;
+  int* B = S.bnd + (int64_t)slot * S.capB;
+  if (lane == 0) S.cand[slot] = p;
+  unsigned long long pbytes = 0, ptests = 0;
+  int nc, nbd, status;
+  grow_region<D, 32>(T, true, p, key, C, nullptr, B, S.capC, S.capB, nc, nbd, status, pbytes, ptests);
+  region_stats<D, 32>(T, true, status, nc, pbytes, ptests);
+  if (lane == 0) {
+    if (status == CAND_OVER) {
+      const int q = atomicAdd(S.nbig, 1);
+      if (q < BIGCAP) S.biglist[q] = slot;
+      else atomicExch(&T.st->overflow_cav, 1);
+    }
+    S.meta[slot] = make_int4(nc, nbd, status, 0);
+  }
+  __syncwarp();
+}
+
+// Small rounds in one CTA: while the active set is at most small_max points
+// (the sample triangulation, the first and the last rounds of every run),
+// every phase of a round runs here between __syncthreads barriers instead of
+// as separate launches.  Up to SMALL_ITERS rounds per launch; the round state
+// is the same control block, so the regular kernels take over (or resume)
+// whenever a round is not small.
+constexpr int SMALL_ITERS = 256;
+
+template <int D>
+__global__ void __launch_bounds__(1024) k_small_rounds(TriView<D> T, EngCtl* ctl, int* cnt, const int* loffd,
+                                                       const int* llist, int* nom, int* walk, CandScratch S) {
+  __shared__ int s_go;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int it = 0; it < SMALL_ITERS; it++) {
+    if (threadIdx.x == 0) s_go = (ctl->done == 0 && ctl->small) ? 1 : 0;
+    __syncthreads();
+    if (!s_go) return;
+    volatile int* vc = cnt;
+    const unsigned round = ctl->round;
+    int* ain = ctl->ain;
+    int* aout = ctl->aout;
+    const int m = ctl->act_n;
+    const int* list = llist + ctl->act_lo;
+    for (int64_t base = warp * 32; base < m; base += nw * 32) activate_warp<D>(T, list, m, ain, cnt + 0, round, base);
+    __syncthreads();
+    const int nact = vc[0];
+    for (int64_t base = warp * 32; base < nact; base += nw * 32)
+      nominate_warp<D>(T, ain, nact, round, nom, cnt + 2, base);
+    __syncthreads();
+    if (threadIdx.x < NBUCKET) vc[8 + threadIdx.x] = threadIdx.x == 0 ? vc[2] : 0;
+    __syncthreads();
+    const int nn = min(vc[2], S.cap);
+    for (int slot = warp; slot < nn; slot += nw) cavity_slot<D>(T, round, S, nom, cnt + 8, slot);
+    __syncthreads();
+    const int nbig = min(vc[5], BIGCAP);
+    for (int q = warp; q < nbig; q += nw) big_region<D>(T, round, S, q);
+    __syncthreads();
+    for (int slot = warp; slot < nn; slot += nw) insert_winner<D>(T, round, S, slot, cnt + 3);
+    __syncthreads();
+    for (int64_t base = warp * 32; base < nact; base += nw * 32)
+      reloc_check_warp<D>(T, ain, nact, aout, cnt + 1, walk, cnt + 4, round + 1, base);
+    __syncthreads();
+    const int nwk = vc[4];
+    for (int i = threadIdx.x; i < nwk; i += blockDim.x) reloc_walk_one<D>(T, walk[i], round + 1);
+    __syncthreads();
+    if (threadIdx.x == 0) round_end_begin(*ctl, cnt, loffd, T.st);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- host
@@ -1071,6 +1231,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
   h0.next_level = next_level;
   h0.last_batch = last_batch;
   h0.last_nact = nact;
+  h0.small_max = c->cfg.small_rounds > 0 ? c->cfg.small_rounds : -1;
   CUDA_OK(cudaMemcpyAsync(ctl, &h0, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
   const int capCand = (int)std::max<int64_t>(1, std::min<int64_t>(npts, int64_t(1) << 22));
   int64_t max_level = 1;
@@ -1123,9 +1284,10 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
         lc.numAttrs = pdl ? 1 : 0;
         return lc;
       };
-      cudaLaunchConfig_t l1 = cfg(ga, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128), l5 = cfg(gn, 256),
-                         l6 = cfg(gr, 128), l7 = cfg(1, 32), l8 = cfg(BIGCAP / 4, 128);
-      l1.numAttrs = 0;   // the body's first node has no kernel before it inside the body
+      cudaLaunchConfig_t l0 = cfg(1, 1024), l1 = cfg(ga, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128),
+                         l5 = cfg(gn, 256), l6 = cfg(gr, 128), l7 = cfg(1, 32), l8 = cfg(BIGCAP / 4, 128);
+      l0.numAttrs = 0;   // the body's first node has no kernel before it inside the body
+      cudaLaunchKernelEx(&l0, k_small_rounds<D>, T, ctl, cnt, loffd, (const int*)llist, nom, walk, S);
       cudaLaunchKernelEx(&l1, k_activate<D>, T, (const int*)llist, 0, (int*)nullptr, cnt + 0, 0u, (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, nom, cnt + 2, cnt + 8,
                          capCand, (const EngCtl*)ctl);
@@ -1160,7 +1322,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     CUDA_OK(cudaMemcpyAsync(&h1, ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
-    c->launches += 1 + 9 * (int64_t)(h1.round - r0 + 1);
+    c->launches += 1 + 10 * (int64_t)(h1.round - r0 + 1);
     if (h1.done == 3 && c->status_host->overflow_cav && grow < 8) {
       // cavities outgrew their scratch: twice the room, same state
       CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));

@@ -139,3 +139,18 @@ def test_large_region_path_matches_oracle(tri, D, k):
     finally:
         tri.configure(cavity_cap=0, base_threshold=2048)
     assert np.array_equal(got, oracle.delaunay(P))
+
+
+@pytest.mark.parametrize("D,kind", [(2, "uniform"), (3, "clustered")])
+def test_single_block_rounds_match_oracle(tri, D, kind):
+    """Every round inside one thread block (small_rounds above n) and none
+    there (small_rounds = -1) give the oracle's DT."""
+    P = pointsets.clustered(6_000, 13) if kind == "clustered" else pointsets.uniform(6_000, D, 13)
+    want = oracle.delaunay(P)
+    for sr in (1_000_000, -1):
+        tri.configure(small_rounds=sr)
+        try:
+            got = tri.triangulate(P, k=1).astype(np.int64)
+        finally:
+            tri.configure(small_rounds=0)
+        assert np.array_equal(got, want), sr
