@@ -77,6 +77,33 @@ def gen_points(w, seed_offset=0):
     return pointsets.clustered(w["n"], w["seed"] + seed_offset)
 
 
+def cavity_fingerprint() -> str:
+    """SHA-1 of the source of the dominant kernel (region growth + k_cavity_w):
+    a stored DRAM-traffic figure only applies to the kernel it was taken on."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1902_07554_gb300", "csrc", "engine.cu")).read()
+    a = src.find("__device__ __forceinline__ void grow_region(")
+    b = src.find("// Second growth of large region")
+    return hashlib.sha1(src[a:b].encode()).hexdigest() if a >= 0 and b > a else ""
+
+
+def stored_cavity_traffic():
+    """DRAM bytes per input point of k_cavity_w<3> over one triangulation, from
+    the ncu capture summarised in profiles/k_cavity_w_traffic.md, if that
+    capture was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_cavity_w_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    import re
+    fp = re.search(r"^fingerprint: ([0-9a-f]{40})$", txt, flags=re.M)
+    bpp = re.search(r"^dram_bytes_per_point: ([0-9.eE+]+)$", txt, flags=re.M)
+    if not fp or not bpp or fp.group(1) != cavity_fingerprint():
+        return None
+    return float(bpp.group(1))
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -440,8 +467,12 @@ def main():
         per_launch_ms = a["ms"] / max(a["launches"], 1)
         bytes_per_launch = a["bytes"] / max(a["launches"], 1)
         achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+        bpp = stored_cavity_traffic() if name == "k_cavity_w<3>" else None
+        traffic = bpp * n / max(a["launches"] / max(args.steps, 1), 1) if bpp else None
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "traffic_source": ("ncu DRAM bytes on uniform3d_200k (host-driven rounds) scaled by points; "
+                                       "profiles/k_cavity_w_traffic.md") if traffic else None,
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                     "share_of_step": a["ms"] / sum(prof_step_ms),
                     "timing": "CUDA events around every launch, K profiled steps after the timed region",

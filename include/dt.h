@@ -95,7 +95,9 @@ typedef struct dt_config {
                             (no launches between their phases); 0 or -1 = never (the default: on
                             GB300 the per-round latency is the phases' memory chains, not the
                             launches, so the graph of separate kernels is as fast or faster) */
-  int reserved[3];
+  int brio_drain;        /* the next BRIO batch is activated when the active set has drained to
+                            1 / brio_drain of the last batch; 0 = automatic (8) */
+  int reserved[2];
 } dt_config;
 
 typedef struct dt_stats {
@@ -279,7 +281,7 @@ DT_API int dt_eval_predicates(dt_ctx* ctx, const double* points, int64_t n, int 
                        const int64_t* gid, int kind, const int32_t* tuples, int64_t m,
                        int8_t* out);
 
-/* Alg. 2, lines 6-8 on given inputs: label every point of P (n x dim) with
+/* Alg. 2 (assignment of the points) on given inputs: label every point of P (n x dim) with
  * block[j] of its exactly nearest sample point S_j (ties: smaller srank),
  * walking the Delaunay graph of S.  All buffers host or device; out n int32. */
 DT_API int dt_label_points(dt_ctx* ctx, const double* P, int64_t n, int dim, const double* S,

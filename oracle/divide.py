@@ -40,7 +40,7 @@ def sample_keys(n: int, seed: int) -> np.ndarray:
 
 
 def sample_ids(n: int, eta: int, seed: int) -> np.ndarray:
-    """Alg. 2, line 1: eta distinct indices uniformly at random, realised as
+    """Alg. 2 (sampling): eta distinct indices uniformly at random, realised as
     the eta smallest (key_i, i) with key_i = splitmix64(splitmix64(seed) xor i).
     Returned sorted by index."""
     keys = sample_keys(n, seed)
@@ -79,7 +79,7 @@ def edge_weights(PS: np.ndarray, E: np.ndarray, kind: str = "log") -> np.ndarray
 
 
 def sample_graph(PS: np.ndarray, gidS: np.ndarray, kind: str = "log"):
-    """Alg. 2, lines 2-3: T = DT(P_S); G = (V = P_S, E = edges of T, omega).
+    """Alg. 2 (sample triangulation and graph): T = DT(P_S); G = (V = P_S, E = edges of T, omega).
     Returns (E (m,2) in sample positions, sorted, u < v; weights)."""
     T = delaunay(PS, gidS)
     pos = {int(g): i for i, g in enumerate(gidS)}
@@ -217,7 +217,7 @@ def cut_weight(E: np.ndarray, w: np.ndarray, block: np.ndarray) -> int:
 # ---------------------------------------------------------------- labels
 def labels(P: np.ndarray, PS: np.ndarray, gidS: np.ndarray, block: np.ndarray,
            idx: np.ndarray | None = None) -> np.ndarray:
-    """Alg. 2, lines 6-8: each point takes the block of its nearest sample
+    """Alg. 2 (assignment of the points): each point takes the block of its nearest sample
     point (exact squared distance; ties: smaller global index).  `idx`
     restricts the computation to a subset of points."""
     Q = P if idx is None else P[idx]
@@ -252,7 +252,7 @@ def kd_labels(P: np.ndarray, k: int) -> np.ndarray:
 
 # ---------------------------------------------------------------- border
 def partial_triangulations(P: np.ndarray, lab: np.ndarray, k: int):
-    """T_i = DT(P_i) with global indices (Alg. 1, line 5); also returns the
+    """T_i = DT(P_i) with global indices (Alg. 1 (partial triangulations)); also returns the
     raw meshes (local ids, -1 = infinite vertex) for the ghost simplices."""
     out = []
     for i in range(k):
@@ -270,7 +270,7 @@ def partial_triangulations(P: np.ndarray, lab: np.ndarray, k: int):
 
 
 def border_exact(P: np.ndarray, lab: np.ndarray, k: int):
-    """Alg. 1, lines 7-18 with the exact primitive and every simplex tested
+    """Alg. 1 (border detection) with the exact primitive and every simplex tested
     (a superset of what a breadth-first search from the hull reaches).
 
     A finite simplex of T_i is a border simplex iff its perturbed circumsphere
@@ -345,7 +345,7 @@ def _coplanar_conflict(P, fin, q) -> bool:
 
 # ---------------------------------------------------------------- merge
 def merge(parts, Bset, VB, P, lab):
-    """Alg. 1, lines 19-28: T = (U T_i) minus B; add s_b in T_B = DT(vertices(B))
+    """Alg. 1 (border triangulation and merging): T = (U T_i) minus B; add s_b in T_B = DT(vertices(B))
     if its vertices lie in more than one partition, or if it equals a border
     simplex.  Returns the merged simplices as a sorted (m, d+1) array."""
     D = P.shape[1]

@@ -49,7 +49,8 @@ class Config(ctypes.Structure):
                 ("base_threshold", ctypes.c_int), ("validate", ctypes.c_int),
                 ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
                 ("first_batch", ctypes.c_int), ("brio_growth", ctypes.c_int),
-                ("small_rounds", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("small_rounds", ctypes.c_int), ("brio_drain", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class KernelProfile(ctypes.Structure):

@@ -1,4 +1,4 @@
-// border.cu -- border detection (Alg. 1, lines 6-18) and vertices(B).
+// border.cu -- border detection (the border step of Alg. 1) and vertices(B).
 //
 // Every live simplex of every partial triangulation T_i is tested (one
 // parallel sweep; a superset of what a breadth-first search from the hull

@@ -38,7 +38,8 @@ static bool cfg_valid(const dt_config* c) {
          c->weight <= 3 && c->lp_rounds >= 0 && c->lp_rounds <= 1000 && c->epsilon >= 0 && c->epsilon <= 10 &&
          c->grid_cell > 0 && c->grid_cell <= 64 && c->base_threshold >= 0 && c->cavity_cap >= 0 &&
          c->cavity_cap <= 4096 && c->first_batch >= 0 &&
-         (c->brio_growth == 0 || (c->brio_growth > 100 && c->brio_growth <= 10000)) && c->small_rounds >= -1;
+         (c->brio_growth == 0 || (c->brio_growth > 100 && c->brio_growth <= 10000)) && c->small_rounds >= -1 &&
+         c->brio_drain >= 0 && c->brio_drain <= 64;
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {

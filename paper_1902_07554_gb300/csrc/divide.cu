@@ -73,7 +73,7 @@ int64_t sample_size(int64_t n, double frac, int D) {
   return eta;
 }
 
-// Alg. 2, line 1: the eta smallest keys splitmix64(splitmix64(seed) ^ i);
+// Alg. 2 (sampling): the eta smallest keys splitmix64(splitmix64(seed) ^ i);
 // writes their indices, ascending, to ids.
 int select_sample(dt_ctx* c, int64_t n, int64_t eta, uint64_t seed, int* ids) {
   cudaStream_t s = c->stream;
@@ -255,7 +255,7 @@ int build_csr(dt_ctx* c, SampleGraph& G) {
   return 0;
 }
 
-// Alg. 2, lines 2-3: G = (P_S, edges of DT(P_S), omega).
+// Alg. 2 (sample triangulation and graph): G = (P_S, edges of DT(P_S), omega).
 int sample_graph(dt_ctx* c, const EngineRun& run, const void* PS, int dim, int kind, SampleGraph& G) {
   cudaStream_t s = c->stream;
   int64_t eta = run.npts;

@@ -123,6 +123,7 @@ struct EngCtl {
   int stalled;         // consecutive rounds without an insertion
   int activated;       // points activated this round
   int done;            // 0 running; 1 finished; 2 device error; 3 stalled; 4 round limit
+  int drain;           // the next batch is activated when the active set is last_batch / drain
   int small;           // 1: the next rounds are small enough for k_small_rounds (one CTA)
   int small_max;       // active points up to which a round counts as small
 };
@@ -936,7 +937,7 @@ __global__ void k_move_count(int* dst, int* src) {
 __device__ void round_begin(EngCtl& C, int* cnt, const int* loffd) {
   int nact = cnt[0];
   int lo = -1, hi = -1;
-  while (C.next_level >= 0 && nact <= C.last_batch / 4) {
+  while (C.next_level >= 0 && nact <= C.last_batch / C.drain) {
     const int l = C.next_level;
     const int m = loffd[l + 1] - loffd[l];
     if (m > 0) {
@@ -1232,6 +1233,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
   h0.last_batch = last_batch;
   h0.last_nact = nact;
   h0.small_max = c->cfg.small_rounds > 0 ? c->cfg.small_rounds : -1;
+  h0.drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
   CUDA_OK(cudaMemcpyAsync(ctl, &h0, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
   const int capCand = (int)std::max<int64_t>(1, std::min<int64_t>(npts, int64_t(1) << 22));
   int64_t max_level = 1;
@@ -1554,6 +1556,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     // Profile and debug runs drive the rounds from the host (events and
     // checks between launches); otherwise one CUDA graph runs every round.
     const bool host_loop = prof || getenv("GDT_DEBUG") || getenv("GDT_CHECK");
+    const int drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
     if (nact > 0)
       k_pick<D><<<(unsigned)ceil_div(nact, 256), 256, (++c->launches, 0), s>>>(T, ain, nact, 1);
     if (!host_loop && (nact > 0 || next_level >= 0)) {
@@ -1565,7 +1568,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     }
     while (nact > 0 || next_level >= 0) {
       // activate the next batch when the active set has drained to a quarter
-      while (next_level >= 0 && nact <= last_batch / 4) {
+      while (next_level >= 0 && nact <= last_batch / drain) {
         int m = (int)(loff[next_level + 1] - loff[next_level]);
         if (m > 0) {
           const int a0 = mark();

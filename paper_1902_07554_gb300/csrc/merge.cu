@@ -1,4 +1,4 @@
-// merge.cu -- the merge of Alg. 1 (lines 19-28): T = (U T_i) \ B, plus every
+// merge.cu -- the merge of Alg. 1: T = (U T_i) \ B, plus every
 // simplex s_b of T_B = DT(vertices(B)) whose vertices lie in more than one
 // partition, or which equals a border simplex.  The equality test is a
 // lookup in a lock-free open-addressing hash table in HBM that stores indices

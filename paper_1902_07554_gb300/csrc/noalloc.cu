@@ -1,4 +1,4 @@
-// noalloc.cu -- sample selection (Alg. 2, line 1) without any allocation.
+// noalloc.cu -- sample selection (Alg. 2 (sampling)) without any allocation.
 //
 // Some callers cannot call cudaMalloc at all: code running under a memory
 // pool it does not own, inside an allocator callback, in a process whose

@@ -390,7 +390,7 @@ __global__ void k_i64_to_i32b(const long long* in, int* out, int64_t n) {
 
 using namespace gdt;
 
-// Alg. 2, lines 6-8 on caller inputs (see include/dt.h).
+// Alg. 2 (assignment of the points) on caller inputs (see include/dt.h).
 extern "C" int dt_label_points(dt_ctx* c, const double* P, int64_t n, int dim, const double* S,
                                const int64_t* srank, const int32_t* block, int64_t m, int32_t* out) {
   if (!c) return DT_E_ARG;

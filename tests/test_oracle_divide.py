@@ -1,6 +1,6 @@
 """Pins for the divide / border / merge references (Alg. 1 and Alg. 2).
 
-The strongest pin: running the paper's merge (Alg. 1, lines 19-28) on the
+The strongest pin: running the paper's merge (Alg. 1 (border triangulation and merging)) on the
 exact border set reproduces DT(P) exactly, for sample-based and kd labels,
 and stays exact when the border set is enlarged arbitrarily (a conservative
 intersection primitive only ever adds simplices).
