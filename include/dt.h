@@ -66,6 +66,9 @@ extern "C" {
 /* Border-detection primitives (Sec. 3.2). */
 #define DT_PRIM_GRID 0       /* occupied uniform-grid cells with a coarse-to-fine hierarchy */
 #define DT_PRIM_BBOX 1       /* one axis-aligned bounding box per partition */
+#define DT_PRIM_POINTS 2     /* the points themselves: a simplex is a border simplex when a point
+                                of another partition lies in its (slightly inflated) circumsphere;
+                                the grid serves as the index (Sec. 3.2, the exact primitive) */
 
 /* Edge weights of the sample graph (Table 1). */
 #define DT_WEIGHT_LOG 0

@@ -22,13 +22,13 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Triangulator", "DTError", "load_library", "declared_symbols", "Config", "Stats",
-           "DIVIDE_SAMPLE", "DIVIDE_KD", "PRIM_GRID", "PRIM_BBOX"]
+           "DIVIDE_SAMPLE", "DIVIDE_KD", "PRIM_GRID", "PRIM_BBOX", "PRIM_POINTS"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "dt.h")
 
 DIVIDE_SAMPLE, DIVIDE_KD = 0, 1
-PRIM_GRID, PRIM_BBOX = 0, 1
+PRIM_GRID, PRIM_BBOX, PRIM_POINTS = 0, 1, 2
 WEIGHTS = {"log": 0, "constant": 1, "inverse": 2, "linear": 3}
 
 ERRORS = {-1: "DT_E_ARG", -2: "DT_E_DUPLICATE", -3: "DT_E_DEGENERATE", -4: "DT_E_NOMEM",

@@ -42,6 +42,11 @@ struct GridView {
   int levels;
   const unsigned long long* mask;
   const unsigned long long* dil; // per cell: OR of the masks of its 3^d block (same layout)
+  // point primitive: the points of each level-0 cell (cell_start[ncell0 + 1], cell_pts[n])
+  const int* cell_start;
+  const int* cell_pts;
+  const void* pts;               // partition-sorted points
+  const int* label;              // partition of each point
 };
 
 template <int D>
@@ -163,8 +168,40 @@ __device__ __forceinline__ bool unit_box_hits(const float* u, float ru2, const i
 // 2^-l as a float, exactly (no division).
 __device__ __forceinline__ float pow2f_neg(int l) { return __int_as_float((127 - l) << 23); }
 
+// Point primitive: does a point of a partition in `others`, held by level-0
+// cell x, lie in the closed shape?  The ball and the halfspace already cover
+// the exact circumsphere / hull side with slack; the tests below add a
+// relative margin for their own rounding.
 template <int D>
-__device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long others) {
+__device__ bool cell_points_hit(const GridView& G, const Shape& S, unsigned long long others, const int* x) {
+  using Pt = typename PT<D>::T;
+  const Pt* P = (const Pt*)G.pts;
+  long long id = 0;
+  for (int c = D - 1; c >= 0; c--) id = id * G.dims[0][c] + x[c];
+  const int b = G.cell_start[id], e = G.cell_start[id + 1];
+  for (int k = b; k < e; k++) {
+    const int q = G.cell_pts[k];
+    const int l = G.label[q];
+    if (l >= 64 || !((others >> l) & 1ull)) continue;
+    const Pt pq = P[q];
+    if (!S.half) {
+      double d2 = 0;
+      for (int c = 0; c < D; c++) { const double d = comp(pq, c) - S.c[c]; d2 += d * d; }
+      if (d2 <= S.r * S.r * (1.0 + 1e-12)) return true;
+    } else {
+      double v = 0, mag = 0;
+      for (int c = 0; c < D; c++) {
+        v += S.n[c] * (comp(pq, c) - S.c[c]);
+        mag += (fabs(S.n[c]) + S.pn[c]) * (fabs(comp(pq, c)) + fabs(S.c[c]));
+      }
+      if (v >= -(S.slack + 1e-12 * mag)) return true;
+    }
+  }
+  return false;
+}
+
+template <int D>
+__device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long others, bool points = false) {
   int lev = G.levels - 1;
   int lo_[3] = {0, 0, 0}, hi_[3] = {0, 0, 0};
   float u[3] = {0, 0, 0}, ru = 0, ru2 = 0;
@@ -237,6 +274,7 @@ __device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long
                 hit = box_hits<D>(S, blo, bhi);
               }
             }
+            if (hit && l == 0 && points) hit = cell_points_hit<D>(G, S, others, f.x);
             if (!hit) { depth--; continue; }
             if (l == 0) return true;
             f.child = 0;
@@ -511,15 +549,17 @@ __global__ void k_border(const typename PT<D>::T* P, BorderArgs A) {
   Shape S;
   bool hit;
   unsigned long long others = A.k >= 64 ? ~(1ull << i) : (((1ull << A.k) - 1) & ~(1ull << i));
+  const bool gridded = A.prim == DT_PRIM_GRID || A.prim == DT_PRIM_POINTS;
+  const bool points = A.prim == DT_PRIM_POINTS;
   if (g >= 0) {
     ghost_halfspace<D>(P, v, g, S);
-    hit = A.prim == DT_PRIM_GRID ? grid_query<D>(A.G, S, others) : bbox_query<D>(A.boxes, A.k, S, others, i);
-  } else if (A.prim == DT_PRIM_GRID && circumball_f32<D>(A.xs, A.xo, v, S) && !grid_query<D>(A.G, S, others)) {
+    hit = gridded ? grid_query<D>(A.G, S, others, points) : bbox_query<D>(A.boxes, A.k, S, others, i);
+  } else if (gridded && circumball_f32<D>(A.xs, A.xo, v, S) && !grid_query<D>(A.G, S, others, points)) {
     hit = false;   // even the larger FP32 ball meets no other partition
   } else if (!circumball<D>(P, v, S)) {
     hit = true;
   } else {
-    hit = A.prim == DT_PRIM_GRID ? grid_query<D>(A.G, S, others) : bbox_query<D>(A.boxes, A.k, S, others, i);
+    hit = gridded ? grid_query<D>(A.G, S, others, points) : bbox_query<D>(A.boxes, A.k, S, others, i);
   }
   if (!hit) return;
   A.bflag[s] = 1;
@@ -531,6 +571,27 @@ __global__ void k_border(const typename PT<D>::T* P, BorderArgs A) {
 __global__ void k_flag_bad_partitions(const int* pinst, const int* inst_status, int64_t n, unsigned char* vflag) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n && inst_status[pinst[i]] != 0) vflag[i] = 1;
+}
+
+// Level-0 cell of each point (the cell k_occupy assigns).
+template <int D>
+__global__ void k_point_cell(const typename PT<D>::T* P, int64_t n, GridView G, int* cell, int* count) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long id = 0;
+  for (int c = D - 1; c >= 0; c--) {
+    double f = (comp(P[i], c) - G.lo[c]) / G.h[0];
+    int v = f < 0 ? 0 : (int)f;
+    id = id * G.dims[0][c] + min(v, G.dims[0][c] - 1);
+  }
+  cell[i] = (int)id;
+  atomicAdd(&count[id], 1);
+}
+__global__ void k_cell_scatter(const int* cell, int64_t n, const int* start, int* fill, int* pts) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = cell[i];
+  pts[start[c] + atomicAdd(&fill[c], 1)] = (int)i;
 }
 
 __global__ void k_boxes_to_double(const unsigned long long* ubox, int k, double* box) {
@@ -585,8 +646,8 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
   if (dim == 2) k_box_reduce<2><<<box_grid(n), 256, (++c->launches, 0), s>>>((const double2*)Ps, pinst, n, ubox);
   else k_box_reduce<3><<<box_grid(n), 256, (++c->launches, 0), s>>>((const double4_32a*)Ps, pinst, n, ubox);
   k_boxes_to_double<<<ceil_div(6 * k, 128), 128, (++c->launches, 0), s>>>(ubox, k, boxes);
-  if (prim == DT_PRIM_GRID) {
-    if (k > 64) return set_err(c, DT_E_ARG, "the grid primitive supports k <= 64");
+  if (prim == DT_PRIM_GRID || prim == DT_PRIM_POINTS) {
+    if (k > 64) return set_err(c, DT_E_ARG, "the grid and point primitives support k <= 64");
     std::vector<double> hb(6 * (size_t)k);
     CUDA_OK(cudaMemcpyAsync(hb.data(), boxes, 8 * 6 * (size_t)k, cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
@@ -656,6 +717,28 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
       else k_dilate_mask<3><<<gl, 256, (++c->launches, 0), s>>>(G, l, mask, dil);
     }
     G.dil = dil;
+    G.cell_start = nullptr;
+    G.cell_pts = nullptr;
+    G.pts = Ps;
+    G.label = pinst;
+    if (prim == DT_PRIM_POINTS) {
+      const long long ncell0 = (long long)G.dims[0][0] * G.dims[0][1] * G.dims[0][2];
+      int* cstart = (int*)pool_get(c, "b.cstart", 4 * (size_t)(ncell0 + 1));
+      int* ccount = (int*)pool_get(c, "b.ccount", 4 * (size_t)(ncell0 + 1));
+      int* cfill = (int*)pool_get(c, "b.cfill", 4 * (size_t)(ncell0 + 1));
+      int* ccell = (int*)pool_get(c, "b.ccell", 4 * (size_t)std::max<int64_t>(n, 1));
+      int* cpts = (int*)pool_get(c, "b.cpts", 4 * (size_t)std::max<int64_t>(n, 1));
+      if (!cstart || !ccount || !cfill || !ccell || !cpts) return set_err(c, DT_E_NOMEM, "cell lists");
+      CUDA_OK(cudaMemsetAsync(ccount, 0, 4 * (size_t)(ncell0 + 1), s));
+      CUDA_OK(cudaMemsetAsync(cfill, 0, 4 * (size_t)(ncell0 + 1), s));
+      if (dim == 2) k_point_cell<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)Ps, n, G, ccell, ccount);
+      else k_point_cell<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)Ps, n, G, ccell, ccount);
+      rc = exclusive_scan_i32(c, ccount, cstart, ncell0 + 1, nullptr);
+      if (rc) return rc;
+      k_cell_scatter<<<g, 256, (++c->launches, 0), s>>>(ccell, n, cstart, cfill, cpts);
+      G.cell_start = cstart;
+      G.cell_pts = cpts;
+    }
   }
   unsigned gs = (unsigned)ceil_div<int64_t>(parts.total_slots, 128);
   if (dim == 2) k_border<2><<<gs, 128, (++c->launches, 0), s>>>((const double2*)Ps, A);

@@ -34,7 +34,7 @@ extern "C" int dt_config_default(dt_config* cfg) {
 }
 
 static bool cfg_valid(const dt_config* c) {
-  return c->divide >= 0 && c->divide <= 1 && c->primitive >= 0 && c->primitive <= 1 && c->weight >= 0 &&
+  return c->divide >= 0 && c->divide <= 1 && c->primitive >= 0 && c->primitive <= 2 && c->weight >= 0 &&
          c->weight <= 3 && c->lp_rounds >= 0 && c->lp_rounds <= 1000 && c->epsilon >= 0 && c->epsilon <= 10 &&
          c->grid_cell > 0 && c->grid_cell <= 64 && c->base_threshold >= 0 && c->cavity_cap >= 0 &&
          c->cavity_cap <= 4096 && c->first_batch >= 0 &&

@@ -53,7 +53,7 @@ def test_k_invariance_sample_divide(tri, D, n, kind, k):
 
 
 @pytest.mark.parametrize("D", [2, 3])
-@pytest.mark.parametrize("divide,prim", [(0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("divide,prim", [(0, 1), (1, 0), (1, 1), (0, 2), (1, 2)])
 def test_k_invariance_divides_and_primitives(tri, D, divide, prim):
     P = pointsets.clustered(20000, 5) if D == 3 else pointsets.normal(20000, 2, 5)
     want = oracle.delaunay(P)
@@ -118,14 +118,18 @@ def test_kd_labels_match_oracle(tri):
 @pytest.mark.parametrize("D,n,k", [(2, 1500, 4), (3, 600, 3)])
 def test_border_vertices_contain_exact_border(tri, D, n, k):
     P = pointsets.uniform(n, D, 21)
-    _cfg(tri, divide=1)
-    tri.triangulate(P, k=k)
-    lab = tri.labels().astype(np.int64)
-    assert np.array_equal(lab, dv.kd_labels(P, k))
-    _, VB, _ = dv.border_exact(P, lab, k)
-    got = set(tri.border_vertices().tolist())
-    assert set(VB.tolist()) <= got
-    assert len(got) < n
+    counts = {}
+    for prim in (0, 2):
+        _cfg(tri, divide=1, primitive=prim)
+        tri.triangulate(P, k=k)
+        lab = tri.labels().astype(np.int64)
+        assert np.array_equal(lab, dv.kd_labels(P, k))
+        _, VB, _ = dv.border_exact(P, lab, k)
+        got = set(tri.border_vertices().tolist())
+        assert set(VB.tolist()) <= got, prim
+        assert len(got) < n
+        counts[prim] = len(got)
+    assert counts[2] <= counts[0]          # the points are a subset of their cells
 
 
 def test_label_points_entry(tri):
