@@ -68,19 +68,23 @@ __device__ __forceinline__ bool verts_ok(const TriView<D>& T, const int4& v) {
   return ok;
 }
 
+// Hint cells of point p: the fine grid (about n_i / 4 cells) and a coarse
+// one (4 x 4 x 4 fine cells per cell), both per instance.
 template <int D>
-__device__ __forceinline__ int hint_cell(const TriView<D>& T, int p) {
+__device__ __forceinline__ void hint_cells(const TriView<D>& T, int p, int& fine, int& coarse) {
   int i = T.pinst[p];
   const double* g = T.glo + 6 * i;
-  const int* d = T.gdim + 4 * i;
+  const int* d = T.gdim + 5 * i;
   typename PT<D>::T q = T.pts[p];
-  int id = 0;
+  int id = 0, id2 = 0;
   for (int c = D - 1; c >= 0; c--) {
     double f = (comp(q, c) - g[c]) * g[3 + c];
     int x = f < 0 ? 0 : (f >= d[c] ? d[c] - 1 : (int)f);
     id = id * d[c] + x;
+    id2 = id2 * ((d[c] + 3) >> 2) + (x >> 2);
   }
-  return d[3] + id;
+  fine = d[3] + id;
+  coarse = d[4] + id2;
 }
 
 template <int D>
@@ -686,7 +690,12 @@ __device__ __forceinline__ void insert_winner(const TriView<D>& T, unsigned roun
     T.state[p] = 1;
     T.loc[p] = base;
     atomicAdd(nwin, 1);
-    if (T.hint) T.hint[hint_cell(T, p)] = base;
+    if (T.hint) {
+      int f, g;
+      hint_cells(T, p, f, g);
+      T.hint[f] = base;
+      T.hint2[g] = base;
+    }
   }
   __syncwarp();
 
@@ -809,7 +818,10 @@ __device__ __forceinline__ void activate_warp(const TriView<D>& T, const int* li
     p = list[idx];
     int s = T.loc[p];
     if (T.hint) {
-      int h = T.hint[hint_cell(T, p)];
+      int f, g;
+      hint_cells(T, p, f, g);
+      int h = T.hint[f];
+      if (!(slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p])) h = T.hint2[g];
       if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
     }
     for (int hop = 0; hop < (1 << 16) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
@@ -1443,11 +1455,11 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     if (npts > 0 && !getenv("GDT_NOHINT")) {
       // grids of about n_i / 4 cells
       double* glo = (double*)pool_get(c, tag + ".glo", 8 * 6 * (size_t)ninst);
-      int* gdim = (int*)pool_get(c, tag + ".gdim", 4 * 4 * (size_t)ninst);
+      int* gdim = (int*)pool_get(c, tag + ".gdim", 4 * 5 * (size_t)ninst);
       if (!glo || !gdim) return set_err(c, DT_E_NOMEM, "hint grids");
       std::vector<double> hg(6 * (size_t)ninst, 0.0);
-      std::vector<int> hd(4 * (size_t)ninst, 1);
-      int64_t cells = 0;
+      std::vector<int> hd(5 * (size_t)ninst, 1);
+      int64_t cells = 0, cells2 = 0;
       for (int i = 0; i < ninst; i++) {
         int64_t ni = poff[i + 1] - poff[i];
         double lo[3], ext[3], vol = 1.0;
@@ -1460,25 +1472,31 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
         }
         double target = std::max<double>(1.0, (double)ni / 4.0);
         double side = nd ? std::pow(vol / target, 1.0 / nd) : 1.0;
-        int64_t ci = 1;
+        int64_t ci = 1, ci2 = 1;
         for (int cc = 0; cc < 3; cc++) {
           int d = 1;
           if (cc < D && ext[cc] > 0 && side > 0) d = (int)std::min(1024.0, std::max(1.0, std::ceil(ext[cc] / side)));
-          hd[4 * i + cc] = d;
+          hd[5 * i + cc] = d;
           hg[6 * i + cc] = cc < D && ni > 0 ? lo[cc] : 0.0;
           hg[6 * i + 3 + cc] = (cc < D && ext[cc] > 0) ? d / ext[cc] : 0.0;
           ci *= d;
+          ci2 *= (d + 3) >> 2;
         }
-        hd[4 * i + 3] = (int)cells;
+        hd[5 * i + 3] = (int)cells;
+        hd[5 * i + 4] = (int)cells2;
         cells += ci;
+        cells2 += ci2;
       }
       int* hint = (int*)pool_get(c, tag + ".hint", 4 * std::max<int64_t>(cells, 1));
-      if (!hint) return set_err(c, DT_E_NOMEM, "hint cells");
+      int* hint2 = (int*)pool_get(c, tag + ".hint2", 4 * std::max<int64_t>(cells2, 1));
+      if (!hint || !hint2) return set_err(c, DT_E_NOMEM, "hint cells");
       CUDA_OK(cudaMemsetAsync(hint, 0xff, 4 * std::max<int64_t>(cells, 1), s));
+      CUDA_OK(cudaMemsetAsync(hint2, 0xff, 4 * std::max<int64_t>(cells2, 1), s));
       CUDA_OK(cudaMemcpyAsync(glo, hg.data(), 8 * 6 * (size_t)ninst, cudaMemcpyHostToDevice, s));
-      CUDA_OK(cudaMemcpyAsync(gdim, hd.data(), 4 * 4 * (size_t)ninst, cudaMemcpyHostToDevice, s));
+      CUDA_OK(cudaMemcpyAsync(gdim, hd.data(), 4 * 5 * (size_t)ninst, cudaMemcpyHostToDevice, s));
       CUDA_OK(cudaStreamSynchronize(s));   // host vectors go out of scope
       T.hint = hint;
+      T.hint2 = hint2;
       T.glo = glo;
       T.gdim = gdim;
     }

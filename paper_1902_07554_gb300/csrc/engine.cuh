@@ -52,8 +52,9 @@ struct TriView {
   // per-instance hint grids: a recently created simplex per cell, used as the
   // start of the walk when a dormant point is activated
   int* hint;                // cells of all instances, -1 = none
+  int* hint2;               // coarse cells (4 x 4 x 4 fine cells each), -1 = none
   const double* glo;        // per instance: grid origin (3) and inverse cell edge (3)
-  const int* gdim;          // per instance: cells per axis (3) and first cell (1)
+  const int* gdim;          // per instance: cells per axis (3), first fine cell, first coarse cell
   const int* toff;          // per instance: first simplex slot
   int ninst;
   unsigned long long* dbg;  // walk statistics (debug runs only; null otherwise)
