@@ -70,6 +70,12 @@ extern "C" {
                                 of another partition lies in its (slightly inflated) circumsphere;
                                 the grid serves as the index (Sec. 3.2, the exact primitive) */
 
+/* Initial blocks of the sample partitioner, refined by label propagation. */
+#define DT_INIT_AUTO 0       /* the default (DT_INIT_KD: lower cut weight and c_v than Hilbert runs
+                                on the uniform and clustered workloads) */
+#define DT_INIT_HILBERT 1    /* k equal ranges of the sample in Hilbert-curve order */
+#define DT_INIT_KD 2         /* the kd median split of the sample (the cuts of DT_DIVIDE_KD) */
+
 /* Edge weights of the sample graph (Table 1). */
 #define DT_WEIGHT_LOG 0
 #define DT_WEIGHT_CONSTANT 1
@@ -100,7 +106,8 @@ typedef struct dt_config {
                             launches, so the graph of separate kernels is as fast or faster) */
   int brio_drain;        /* the next BRIO batch is activated when the active set has drained to
                             1 / brio_drain of the last batch; 0 = automatic (8) */
-  int reserved[2];
+  int partition_init;    /* DT_INIT_*: initial blocks of the sample partitioner */
+  int reserved[1];
 } dt_config;
 
 typedef struct dt_stats {
@@ -292,7 +299,8 @@ DT_API int dt_label_points(dt_ctx* ctx, const double* P, int64_t n, int dim, con
 
 /* k-way partition of a sample graph given as an edge list (E rows u < v,
  * int64 weights) over eta vertices with coordinates S (eta x dim): the
- * deterministic Hilbert-runs + label-propagation partitioner.  out: eta int32. */
+ * deterministic initial blocks of the context's partition_init (Hilbert runs
+ * or the kd median split) refined by label propagation.  out: eta int32. */
 DT_API int dt_partition_graph(dt_ctx* ctx, const double* S, int64_t eta, int dim, const int32_t* E,
                        const int64_t* w, int64_t m, int k, double eps, int rounds,
                        int32_t* out);

@@ -147,12 +147,14 @@ def partition_bounds(eta: int, k: int, eps: float):
 
 
 def partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float = 0.05,
-              rounds: int = 16) -> np.ndarray:
+              rounds: int = 16, init: str = "kd") -> np.ndarray:
     """Size-constrained k-way partition of the sample graph (stands in for
     KaHIP, which is not available).  Deterministic:
 
-    1. initial blocks: sample vertices in Hilbert order (ties: vertex index)
-       cut into k consecutive runs, block = floor(rank * k / eta);
+    1. initial blocks: with init "hilbert", sample vertices in Hilbert order
+       (ties: vertex index) cut into k consecutive runs,
+       block = floor(rank * k / eta); with init "kd", the kd median split of
+       the sample points (`kd_labels`, ties: vertex index);
     2. `rounds` rounds of synchronous label propagation.  In round r only
        vertices with v % 2 == r % 2 move.  A vertex's target is the
        neighbouring block with the largest total edge weight to it (ties:
@@ -164,12 +166,15 @@ def partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float =
     eta, D = PS.shape
     if k <= 1:
         return np.zeros(eta, dtype=np.int64)
-    bits = hilbert_bits(D)
-    q = quantize(PS, bits)
-    keys = np.array([hilbert_key(q[i], bits) for i in range(eta)], dtype=np.int64)
-    order = np.lexsort((np.arange(eta), keys))
-    block = np.empty(eta, dtype=np.int64)
-    block[order] = (np.arange(eta) * k) // eta
+    if init == "kd":
+        block = kd_labels(PS, k)
+    else:
+        bits = hilbert_bits(D)
+        q = quantize(PS, bits)
+        keys = np.array([hilbert_key(q[i], bits) for i in range(eta)], dtype=np.int64)
+        order = np.lexsort((np.arange(eta), keys))
+        block = np.empty(eta, dtype=np.int64)
+        block[order] = (np.arange(eta) * k) // eta
     lmin, lmax = partition_bounds(eta, k, eps)
     # adjacency lists with weights
     nbrs = [[] for _ in range(eta)]

@@ -22,7 +22,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Triangulator", "DTError", "load_library", "declared_symbols", "Config", "Stats",
-           "DIVIDE_SAMPLE", "DIVIDE_KD", "PRIM_GRID", "PRIM_BBOX", "PRIM_POINTS"]
+           "DIVIDE_SAMPLE", "DIVIDE_KD", "PRIM_GRID", "PRIM_BBOX", "PRIM_POINTS", "INITS"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "dt.h")
@@ -30,6 +30,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "dt.h")
 DIVIDE_SAMPLE, DIVIDE_KD = 0, 1
 PRIM_GRID, PRIM_BBOX, PRIM_POINTS = 0, 1, 2
 WEIGHTS = {"log": 0, "constant": 1, "inverse": 2, "linear": 3}
+INITS = {"auto": 0, "hilbert": 1, "kd": 2}
 
 ERRORS = {-1: "DT_E_ARG", -2: "DT_E_DUPLICATE", -3: "DT_E_DEGENERATE", -4: "DT_E_NOMEM",
           -5: "DT_E_TIMEOUT", -6: "DT_E_OVERFLOW", -7: "DT_E_CUDA", -8: "DT_E_RANGE",
@@ -50,7 +51,7 @@ class Config(ctypes.Structure):
                 ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
                 ("first_batch", ctypes.c_int), ("brio_growth", ctypes.c_int),
                 ("small_rounds", ctypes.c_int), ("brio_drain", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("partition_init", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class KernelProfile(ctypes.Structure):
@@ -172,6 +173,8 @@ class Triangulator:
         for k, v in config.items():
             if k == "weight" and isinstance(v, str):
                 v = WEIGHTS[v]
+            if k == "partition_init" and isinstance(v, str):
+                v = INITS[v]
             setattr(cfg, k, v)
         self._cfg = cfg
         rc = self.L.dt_create(ctypes.byref(self.ctx), device, stream, ctypes.byref(cfg))
@@ -187,6 +190,8 @@ class Triangulator:
         for k, v in config.items():
             if k == "weight" and isinstance(v, str):
                 v = WEIGHTS[v]
+            if k == "partition_init" and isinstance(v, str):
+                v = INITS[v]
             setattr(self._cfg, k, v)
         self._check(self.L.dt_set_config(self.ctx, ctypes.byref(self._cfg)))
 

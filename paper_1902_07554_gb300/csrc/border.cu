@@ -23,6 +23,9 @@
 namespace gdt {
 
 constexpr int MAXLEV = 16;
+// Point primitive: points of other partitions one simplex may test before the
+// query answers "hit" (always safe: the border may only grow).
+constexpr int POINT_BUDGET = 1024;
 
 // Order-preserving map of doubles to unsigned integers (for atomic min/max).
 __device__ __forceinline__ unsigned long long orderable_key(double x) {
@@ -165,6 +168,18 @@ __device__ __forceinline__ bool unit_box_hits(const float* u, float ru2, const i
   return d2 <= ru2;
 }
 
+// Is the whole cell x of edge w inside the ball (its farthest corner within ru)?
+template <int D>
+__device__ __forceinline__ bool unit_box_inside(const float* u, float ru2, const int* x, float w) {
+  float d2 = 0;
+  for (int c = 0; c < D; c++) {
+    const float lo = x[c] * w, hi = lo + w;
+    const float v = fmaxf(u[c] - lo, hi - u[c]);
+    d2 = fmaf(v, v, d2);
+  }
+  return d2 <= ru2;
+}
+
 // 2^-l as a float, exactly (no division).
 __device__ __forceinline__ float pow2f_neg(int l) { return __int_as_float((127 - l) << 23); }
 
@@ -173,12 +188,15 @@ __device__ __forceinline__ float pow2f_neg(int l) { return __int_as_float((127 -
 // the exact circumsphere / hull side with slack; the tests below add a
 // relative margin for their own rounding.
 template <int D>
-__device__ bool cell_points_hit(const GridView& G, const Shape& S, unsigned long long others, const int* x) {
+__device__ bool cell_points_hit(const GridView& G, const Shape& S, unsigned long long others, const int* x,
+                                int& budget) {
   using Pt = typename PT<D>::T;
   const Pt* P = (const Pt*)G.pts;
   long long id = 0;
   for (int c = D - 1; c >= 0; c--) id = id * G.dims[0][c] + x[c];
   const int b = G.cell_start[id], e = G.cell_start[id + 1];
+  budget -= e - b;
+  if (budget < 0) return true;   // too many points near the shape: answer "hit"
   for (int k = b; k < e; k++) {
     const int q = G.cell_pts[k];
     const int l = G.label[q];
@@ -247,7 +265,7 @@ __device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long
   }
   struct Frame { int x[3]; int child; };
   Frame st[MAXLEV + 1];
-  int visits = 0;
+  int visits = 0, budget = POINT_BUDGET;
   for (int z = (D == 3 ? lo_[2] : 0); z <= (D == 3 ? hi_[2] : 0); z++)
     for (int y = lo_[1]; y <= hi_[1]; y++)
       for (int x = lo_[0]; x <= hi_[0]; x++) {
@@ -262,6 +280,8 @@ __device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long
             if (hit) {
               if (!S.half) {
                 hit = unit_box_hits<D>(u, ru2, f.x, (float)(1 << l));
+                // a cell inside the ball holding a point of another partition settles it
+                if (hit && unit_box_inside<D>(u, ru2, f.x, (float)(1 << l))) return true;
               } else {
                 if (++visits > 64) return true;
                 double blo[3], bhi[3];
@@ -274,7 +294,7 @@ __device__ bool grid_query(const GridView& G, const Shape& S, unsigned long long
                 hit = box_hits<D>(S, blo, bhi);
               }
             }
-            if (hit && l == 0 && points) hit = cell_points_hit<D>(G, S, others, f.x);
+            if (hit && l == 0 && points) hit = cell_points_hit<D>(G, S, others, f.x, budget);
             if (!hit) { depth--; continue; }
             if (l == 0) return true;
             f.child = 0;

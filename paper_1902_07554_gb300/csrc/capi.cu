@@ -39,7 +39,7 @@ static bool cfg_valid(const dt_config* c) {
          c->grid_cell > 0 && c->grid_cell <= 64 && c->base_threshold >= 0 && c->cavity_cap >= 0 &&
          c->cavity_cap <= 4096 && c->first_batch >= 0 &&
          (c->brio_growth == 0 || (c->brio_growth > 100 && c->brio_growth <= 10000)) && c->small_rounds >= -1 &&
-         c->brio_drain >= 0 && c->brio_drain <= 64;
+         c->brio_drain >= 0 && c->brio_drain <= 64 && c->partition_init >= 0 && c->partition_init <= 2;
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {

@@ -400,7 +400,8 @@ void partition_bounds(int64_t eta, int k, double eps, int* lmin, int* lmax) {
 
 // Size-constrained k-way partition (see the oracle's partition() for the
 // exact rule); block[] receives eta labels.
-int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, double eps, int rounds, int* block) {
+int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, double eps, int rounds, int init,
+                    int* block) {
   cudaStream_t s = c->stream;
   int64_t eta = G.eta;
   if (k <= 1) { CUDA_OK(cudaMemsetAsync(block, 0, 4 * eta, s)); return 0; }
@@ -415,13 +416,20 @@ int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, d
   int* sizes = (int*)pool_get(c, "p.sizes", 4 * 256);
   if (!keys || !idx || !target || !source || !rankT || !rankS || !rankB || !sizes)
     return set_err(c, DT_E_NOMEM, "partition buffers");
-  int bits = dim == 2 ? 16 : 10;
   unsigned g = (unsigned)ceil_div<int64_t>(eta, 256);
-  if (dim == 2) k_hilbert<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)PS, eta, G.box, bits, keys, idx);
-  else k_hilbert<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)PS, eta, G.box, bits, keys, idx);
-  int rc = radix_sort_pairs<uint32_t, int>(c, keys, idx, eta, bits * dim, "p.sort");
-  if (rc) return rc;
-  k_initial_blocks<<<g, 256, (++c->launches, 0), s>>>(idx, eta, k, block);
+  int rc;
+  if (init == DT_INIT_KD || init == DT_INIT_AUTO) {
+    // the comparator's median cuts, applied to the sample
+    rc = kd_divide(c, dim, PS, eta, k, block, "pkd");
+    if (rc) return rc;
+  } else {
+    int bits = dim == 2 ? 16 : 10;
+    if (dim == 2) k_hilbert<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)PS, eta, G.box, bits, keys, idx);
+    else k_hilbert<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)PS, eta, G.box, bits, keys, idx);
+    rc = radix_sort_pairs<uint32_t, int>(c, keys, idx, eta, bits * dim, "p.sort");
+    if (rc) return rc;
+    k_initial_blocks<<<g, 256, (++c->launches, 0), s>>>(idx, eta, k, block);
+  }
   int lmin, lmax;
   partition_bounds(eta, k, eps, &lmin, &lmax);
   for (int r = 0; r < rounds; r++) {
@@ -614,12 +622,13 @@ __global__ void k_kd_assign(const int* idx, int64_t n, const int* nstart, const 
   label[p] = pos < nml[node] ? node : node + nkl[node];
 }
 
-int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label) {
+int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label, const char* tag) {
   cudaStream_t s = c->stream;
-  unsigned long long* keys = (unsigned long long*)pool_get(c, "kd.keys", 8 * n);
-  int* idx = (int*)pool_get(c, "kd.idx", 4 * n);
-  uint32_t* nkeys = (uint32_t*)pool_get(c, "kd.nkeys", 4 * n);
-  int* tabs = (int*)pool_get(c, "kd.tabs", 4 * 4 * (size_t)k);
+  const std::string t(tag);
+  unsigned long long* keys = (unsigned long long*)pool_get(c, t + ".keys", 8 * n);
+  int* idx = (int*)pool_get(c, t + ".idx", 4 * n);
+  uint32_t* nkeys = (uint32_t*)pool_get(c, t + ".nkeys", 4 * n);
+  int* tabs = (int*)pool_get(c, t + ".tabs", 4 * 4 * (size_t)k);
   if (!keys || !idx || !nkeys || !tabs) return set_err(c, DT_E_NOMEM, "kd buffers");
   CUDA_OK(cudaMemsetAsync(label, 0, 4 * n, s));
   struct Node { int first, kk; int64_t size; };
@@ -653,10 +662,10 @@ int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label) {
     int cdim = depth % dim;
     if (dim == 2) k_kd_keys<2><<<g, 256, (++c->launches, 0), s>>>((const double2*)P, n, cdim, keys, idx);
     else k_kd_keys<3><<<g, 256, (++c->launches, 0), s>>>((const double4_32a*)P, n, cdim, keys, idx);
-    int rc = radix_sort_pairs<unsigned long long, int>(c, keys, idx, n, 64, "kd.s1");
+    int rc = radix_sort_pairs<unsigned long long, int>(c, keys, idx, n, 64, t + ".s1");
     if (rc) return rc;
     k_kd_nodekeys<<<g, 256, (++c->launches, 0), s>>>(idx, label, n, nkeys);
-    rc = radix_sort_pairs<uint32_t, int>(c, nkeys, idx, n, nbits, "kd.s2");
+    rc = radix_sort_pairs<uint32_t, int>(c, nkeys, idx, n, nbits, t + ".s2");
     if (rc) return rc;
     k_kd_assign<<<g, 256, (++c->launches, 0), s>>>(idx, n, tabs, tabs + k, tabs + 2 * k, tabs + 3 * k, label);
     nodes = next;

@@ -25,11 +25,12 @@ int sample_graph(dt_ctx* c, const EngineRun& run, const void* PS, int dim, int k
 int build_csr(dt_ctx* c, SampleGraph& G);
 int graph_bbox(dt_ctx* c, int dim, const void* PS, int64_t eta, double* box);
 void partition_bounds(int64_t eta, int k, double eps, int* lmin, int* lmax);
-int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, double eps, int rounds, int* block);
+int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, double eps, int rounds, int init,
+                    int* block);
 int cut_weight(dt_ctx* c, const SampleGraph& G, const int* block, long long* out);
 int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, const int* srank, const SampleGraph& G,
                  const int* block, int* label, int* nearest);
-int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label);
+int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label, const char* tag = "kd");
 int scatter_by_label(dt_ctx* c, int dim, const void* P, const int* label, int64_t n, int k, void* Ps, int* gid,
                      int* pinst, std::vector<int64_t>& poff, std::vector<int64_t>& sizes_out);
 __global__ void k_fill_int(int* a, int64_t n, int v);

@@ -123,7 +123,7 @@ static int run_dc(dt_ctx* c, const void* P, int64_t n, int dim, int k, double fr
     rc = sample_graph(c, c->run_sample, PS, dim, cfg.weight, G);
     if (rc) return rc;
     cudaEventRecord(c->ev[3], s);
-    rc = partition_graph(c, PS, dim, G, k, cfg.epsilon, cfg.lp_rounds, block);
+    rc = partition_graph(c, PS, dim, G, k, cfg.epsilon, cfg.lp_rounds, cfg.partition_init, block);
     if (rc) return rc;
     long long cut = 0;
     rc = cut_weight(c, G, block, &cut);
@@ -453,7 +453,7 @@ extern "C" int dt_partition_graph(dt_ctx* c, const double* S, int64_t eta, int d
   if (rc) return rc;
   rc = build_csr(c, G);
   if (rc) return rc;
-  rc = partition_graph(c, dS, dim, G, k, eps, rounds, block);
+  rc = partition_graph(c, dS, dim, G, k, eps, rounds, c->cfg.partition_init, block);
   if (rc) return rc;
   rc = check_status(c, "partition graph");
   if (rc) return rc;

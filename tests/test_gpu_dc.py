@@ -147,6 +147,13 @@ def test_partition_graph_entry(tri):
     P = pointsets.normal(5000, 2, 12)
     ids = dv.sample_ids(5000, 500, 3)
     E, w = dv.sample_graph(P[ids], ids)
-    for k in (3, 8):
+    for k in (3, 8, 16):
         got = tri.partition_graph(P[ids], E, w, k, 0.05, 16)
-        assert np.array_equal(got.astype(np.int64), dv.partition(P[ids], E, w, k))
+        assert np.array_equal(got.astype(np.int64), dv.partition(P[ids], E, w, k, init="kd"))
+    tri.configure(partition_init="hilbert")
+    try:
+        for k in (3, 8):
+            got = tri.partition_graph(P[ids], E, w, k, 0.05, 16)
+            assert np.array_equal(got.astype(np.int64), dv.partition(P[ids], E, w, k, init="hilbert"))
+    finally:
+        tri.configure(partition_init="auto")

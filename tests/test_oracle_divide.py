@@ -71,19 +71,36 @@ def test_graph_is_sample_dt_edges(orc):
     assert np.all(w >= 1)
 
 
+@pytest.mark.parametrize("init", ["hilbert", "kd"])
 @pytest.mark.parametrize("D,k", [(2, 4), (2, 7), (3, 16)])
-def test_partition_balance_and_cut(orc, D, k):
+def test_partition_balance_and_cut(orc, D, k, init):
     P = pointsets.clustered(3000, 5) if D == 3 else pointsets.normal(3000, 2, 5)
     ids = dv.sample_ids(3000, 400, 2)
     PS = P[ids]
     E, w = dv.sample_graph(PS, ids)
-    b0 = dv.partition(PS, E, w, k, rounds=0)
-    b = dv.partition(PS, E, w, k)
+    b0 = dv.partition(PS, E, w, k, rounds=0, init=init)
+    b = dv.partition(PS, E, w, k, init=init)
     lmin, lmax = dv.partition_bounds(400, k, 0.05)
     sizes = np.bincount(b, minlength=k)
     assert sizes.max() <= lmax and sizes.min() >= lmin
     assert dv.cut_weight(E, w, b) <= dv.cut_weight(E, w, b0)
-    assert np.array_equal(b, dv.partition(PS, E, w, k))
+    assert np.array_equal(b, dv.partition(PS, E, w, k, init=init))
+    if init == "kd":
+        # before refinement: the median boxes of the sample, sizes within one
+        assert np.array_equal(b0, dv.kd_labels(PS, k))
+        s0 = np.bincount(b0, minlength=k)
+        assert s0.max() - s0.min() <= 1
+
+
+def test_partition_initial_blocks_by_hand():
+    """Eight points on a line, k = 2, no refinement: Hilbert runs and the kd
+    median split both put the four leftmost points in block 0."""
+    PS = np.array([[x, 0.1 * (x % 2)] for x in (5, 1, 7, 3, 0, 6, 2, 4)], dtype=np.float64)
+    E = np.zeros((0, 2), dtype=np.int64)
+    w = np.zeros(0, dtype=np.int64)
+    want = (PS[:, 0] >= 4).astype(np.int64)
+    assert np.array_equal(dv.partition(PS, E, w, 2, rounds=0, init="kd"), want)
+    assert np.array_equal(dv.partition(PS, E, w, 2, rounds=0, init="hilbert"), want)
 
 
 def test_kd_labels_are_median_boxes():
