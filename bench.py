@@ -331,6 +331,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform3d_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--divide", default="sample", choices=["sample", "kd"])
+    ap.add_argument("--recursive", action="store_true",
+                    help="recursive bisection (log2 k bisections, k - 1 merges) instead of direct k-way")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-rounds", action="store_true",
                     help="drive every insertion round from the host (profile mode) in all steps, so that a "
@@ -359,7 +361,7 @@ def main():
     torch.cuda.set_stream(stream)
     # neighbors=1: the merge's neighbourhood update runs inside every step
     tri = Triangulator(local, stream=stream.cuda_stream, divide=0 if args.divide == "sample" else 1,
-                       profile=1 if args.host_rounds else 0, neighbors=1)
+                       profile=1 if args.host_rounds else 0, neighbors=1, recursive=1 if args.recursive else 0)
     P = gen_points(w, seed_offset=rank)
     n = w["n"]
     P_dev = torch.from_numpy(P).to(f"cuda:{local}")
@@ -490,7 +492,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "dim": w["dim"], "k": w["k"], "sample_frac": w["frac"],
-                   "divide": args.divide, "primitive": "grid", "weight": "log", "neighbors": True,
+                   "divide": args.divide + (" recursive bisection" if args.recursive else ""),
+                   "primitive": "grid", "weight": "log", "neighbors": True,
                    "rounds": "host-driven (profile mode)" if args.host_rounds else "one CUDA graph per engine run",
                    "l2": "flushed before every step (256 MiB write); working set > L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},

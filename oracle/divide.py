@@ -255,6 +255,70 @@ def kd_labels(P: np.ndarray, k: int) -> np.ndarray:
     return lab
 
 
+# ---------------------------------------------------------------- recursive bisection
+def recursive_labels(P: np.ndarray, k: int, frac: float, seed: int, eps: float = 0.05, rounds: int = 16,
+                     init: str = "kd", weight: str = "log") -> np.ndarray:
+    """Recursive bisection with the sample divide (Sec. 3.3): Alg. 2 applied
+    log2 k times with k' = 2.  A node is named by its first leaf; it holds the
+    points labelled with that leaf, in ascending global index, and its local
+    index of a point is the point's rank there.  At depth t every node with kk
+    leaves draws its own sample (sample_ids over its points with seed + t,
+    local indices, which also rank the sample's perturbation and nearest-point
+    ties), triangulates it, partitions the sample graph into 2 and sends each
+    point to the first leaf of its side (first, or first + kk / 2).
+    k must be a power of two.  Returns the leaf of every point."""
+    n, D = P.shape
+    L = int(k).bit_length() - 1
+    if k < 1 or (1 << L) != k:
+        raise ValueError("k must be a power of two")
+    lab = np.zeros(n, dtype=np.int64)
+    for depth in range(L):
+        kk = k >> depth
+        new = lab.copy()
+        for first in range(0, k, kk):
+            ids = np.nonzero(lab == first)[0]
+            m = len(ids)
+            eta = sample_size(m, frac, D)
+            sids = sample_ids(m, eta, seed + depth)
+            PN = P[ids]
+            PS = PN[sids]
+            E, w = sample_graph(PS, sids, weight)
+            block = partition(PS, E, w, 2, eps, rounds, init)
+            side = labels(PN, PS, sids, block)
+            new[ids] = first + (kk // 2) * side
+        lab = new
+    return lab
+
+
+def recursive_merges(P: np.ndarray, lab: np.ndarray, k: int):
+    """The k - 1 merges of recursive bisection, bottom-up (Sec. 3.3): at level
+    h (1..log2 k) the parts are the leaves with the h - 1 low bits dropped, and
+    node v merges parts 2v and 2v + 1 by Alg. 1 with k = 2 on its own points
+    (exact border, border triangulation, merge rule).  Returns the merged
+    simplices of the root (global indices, sorted rows) and, per level, the
+    list of the nodes' |vertices(B)|."""
+    n, D = P.shape
+    L = int(k).bit_length() - 1
+    sizes = []
+    rows = None
+    for h in range(1, L + 1):
+        part = lab >> (h - 1)
+        level = []
+        merged = []
+        for v in range((k >> (h - 1)) // 2):
+            ids = np.nonzero((part >> 1) == v)[0]
+            side = (part[ids] & 1).astype(np.int64)
+            PV = P[ids]
+            Bset, VB, parts = border_exact(PV, side, 2)
+            level.append(len(VB))
+            T = merge(parts, Bset, VB, PV, side)
+            merged.append(ids[T])
+        sizes.append(level)
+        rows = np.concatenate(merged).reshape(-1, D + 1)
+    order = np.lexsort(rows.T[::-1])
+    return rows[order], sizes
+
+
 # ---------------------------------------------------------------- border
 def partial_triangulations(P: np.ndarray, lab: np.ndarray, k: int):
     """T_i = DT(P_i) with global indices (Alg. 1 (partial triangulations)); also returns the

@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
                 ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
                 ("first_batch", ctypes.c_int), ("brio_growth", ctypes.c_int),
                 ("small_rounds", ctypes.c_int), ("brio_drain", ctypes.c_int),
-                ("partition_init", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("partition_init", ctypes.c_int), ("recursive", ctypes.c_int)]
 
 
 class KernelProfile(ctypes.Structure):

@@ -550,6 +550,7 @@ struct BorderArgs {
   unsigned char* bflag;    // per slot
   unsigned char* vflag;    // per (partition-sorted) point
   int* nborder;            // finite border simplices counter
+  const unsigned long long* others;   // per instance: partitions it is tested against (null: all others)
 };
 
 template <int D>
@@ -568,7 +569,9 @@ __global__ void k_border(const typename PT<D>::T* P, BorderArgs A) {
   for (int j = 0; j <= D; j++) if (t[j] == INF_V) g = j;
   Shape S;
   bool hit;
-  unsigned long long others = A.k >= 64 ? ~(1ull << i) : (((1ull << A.k) - 1) & ~(1ull << i));
+  unsigned long long others = A.others ? A.others[i]
+                                       : (A.k >= 64 ? ~(1ull << i) : (((1ull << A.k) - 1) & ~(1ull << i)));
+  if (!others) return;
   const bool gridded = A.prim == DT_PRIM_GRID || A.prim == DT_PRIM_POINTS;
   const bool points = A.prim == DT_PRIM_POINTS;
   if (g >= 0) {
@@ -624,7 +627,8 @@ __global__ void k_boxes_to_double(const unsigned long long* ubox, int k, double*
 }
 
 int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, const int* pinst, int k, double cell,
-                  int prim, unsigned char** bflag_out, unsigned char** vflag_out, int64_t* nborder) {
+                  int prim, unsigned char** bflag_out, unsigned char** vflag_out, int64_t* nborder,
+                  const std::vector<unsigned long long>* others) {
   cudaStream_t s = c->stream;
   int64_t n = parts.npts;
   unsigned char* bflag = (unsigned char*)pool_get(c, "b.bflag", std::max<int64_t>(parts.total_slots, 1));
@@ -659,6 +663,14 @@ int border_detect(dt_ctx* c, int dim, const EngineRun& parts, const void* Ps, co
   A.bflag = bflag;
   A.vflag = vflag;
   A.nborder = cnt;
+  A.others = nullptr;
+  if (others) {
+    if ((int)others->size() < parts.ninst) return set_err(c, DT_E_INTERNAL, "partition masks");
+    unsigned long long* om = (unsigned long long*)pool_get(c, "b.others", 8 * (size_t)parts.ninst);
+    if (!om) return set_err(c, DT_E_NOMEM, "partition masks");
+    CUDA_OK(cudaMemcpyAsync(om, others->data(), 8 * (size_t)parts.ninst, cudaMemcpyHostToDevice, s));
+    A.others = om;
+  }
   memset(&A.G, 0, sizeof(A.G));
   // per-partition boxes (bbox primitive and the grid's extent)
   CUDA_OK(cudaMemsetAsync(ubox, 0, 8 * 6 * (size_t)k, s));

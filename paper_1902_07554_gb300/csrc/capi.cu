@@ -39,7 +39,8 @@ static bool cfg_valid(const dt_config* c) {
          c->grid_cell > 0 && c->grid_cell <= 64 && c->base_threshold >= 0 && c->cavity_cap >= 0 &&
          c->cavity_cap <= 4096 && c->first_batch >= 0 &&
          (c->brio_growth == 0 || (c->brio_growth > 100 && c->brio_growth <= 10000)) && c->small_rounds >= -1 &&
-         c->brio_drain >= 0 && c->brio_drain <= 64 && c->partition_init >= 0 && c->partition_init <= 2;
+         c->brio_drain >= 0 && c->brio_drain <= 64 && c->partition_init >= 0 && c->partition_init <= 2 &&
+         (c->recursive == 0 || c->recursive == 1);
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {
@@ -339,7 +340,8 @@ extern "C" int dt_get_simplices_device(dt_ctx* c, const int32_t** dptr, int64_t*
 // Neighbourhood update of the merge (see include/dt.h).
 extern "C" int dt_get_neighbors(dt_ctx* c, int32_t* out, int64_t capacity, int64_t* count) {
   if (!c || !count) return DT_E_ARG;
-  if (!c->links_ok) return set_err(c, DT_E_ARG, "no single triangulation result (call dt_triangulate first)");
+  if (!c->links_ok && !c->rows_only)
+    return set_err(c, DT_E_ARG, "no single triangulation result (call dt_triangulate first)");
   *count = c->nout;
   if (!out) return DT_OK;
   if (capacity < c->nout) return set_err(c, DT_E_ARG, "capacity too small");

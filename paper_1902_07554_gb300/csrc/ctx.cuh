@@ -46,6 +46,7 @@ struct dt_ctx {
   // provenance of the output rows (neighbourhood update) and its result
   gdt::LinkSources links;
   bool links_ok = false;
+  bool rows_only = false;                // a single triangulation without link sources (recursive bisection)
   int32_t* nbr = nullptr;                // device, (dim+1) per output row
   bool nbr_ok = false;
   // batched call: per-instance row offsets (count+1) and status

@@ -14,7 +14,7 @@ namespace gdt {
 
 
 // Base case of Alg. 1 (n < N, or k = 1): one triangulation of all points.
-static int run_direct(dt_ctx* c, const void* P, int64_t n, int dim) {
+int run_direct(dt_ctx* c, const void* P, int64_t n, int dim) {
   cudaStream_t s = c->stream;
   int* gid = (int*)pool_get(c, "pl.gid", 4 * n);
   int* pinst = (int*)pool_get(c, "pl.pinst", 4 * n);
@@ -72,7 +72,7 @@ __global__ void k_flag_by_gid(const unsigned char* vflag, const int* gid, int64_
 }
 
 // Indices i with flag[i] set, ascending; *m receives the count.
-static int compact_flags(dt_ctx* c, const unsigned char* flag, int64_t n, int* out, int64_t* m, const char* tag) {
+int compact_flags(dt_ctx* c, const unsigned char* flag, int64_t n, int* out, int64_t* m, const char* tag) {
   int* f32 = (int*)pool_get(c, std::string(tag) + ".f", 4 * std::max<int64_t>(n, 1));
   int* pos = (int*)pool_get(c, std::string(tag) + ".p", 4 * std::max<int64_t>(n, 1));
   if (!f32 || !pos) return set_err(c, DT_E_NOMEM, "compaction");
@@ -280,6 +280,7 @@ __global__ void k_rows_to_local(int32_t* rows, int64_t nrows, const long long* o
 int run_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count, int dim) {
   cudaStream_t s = c->stream;
   c->links_ok = false;
+  c->rows_only = false;
   c->nbr_ok = false;
   int64_t n = offsets[count];
   std::vector<int64_t> poff(offsets, offsets + count + 1);
@@ -338,8 +339,16 @@ int run_batch(dt_ctx* c, const double* points, const int64_t* offsets, int count
 // Neighbourhood update of the last result (once per result).
 int ensure_neighbors(dt_ctx* c) {
   if (c->nbr_ok) return 0;
-  if (!c->links_ok) return set_err(c, DT_E_ARG, "no single triangulation result to link");
-  int rc = neighbor_update(c, c->dim, c->out, c->nout, c->links, &c->nbr);
+  int rc;
+  if (c->links_ok) {
+    rc = neighbor_update(c, c->dim, c->out, c->nout, c->links, &c->nbr);
+  } else if (c->rows_only) {   // a single triangulation without link sources: every facet through the hash
+    int64_t nm = 0;
+    rc = match_all_facets(c, c->dim, c->out, c->nout, &c->nbr, &nm);
+    if (!rc && nm) rc = set_err(c, DT_E_INTERNAL, "a facet in more than two simplices");
+  } else {
+    return set_err(c, DT_E_ARG, "no single triangulation result to link");
+  }
   if (rc) return rc;
   c->nbr_ok = true;
   return 0;
@@ -348,10 +357,13 @@ int ensure_neighbors(dt_ctx* c) {
 int run_pipeline(dt_ctx* c, const double* points, int64_t n, int dim, int k, double frac) {
   void* P = nullptr;
   c->links_ok = false;
+  c->rows_only = false;
   c->nbr_ok = false;
   int rc = stage_points(c, points, n, dim, &P, "in");
   if (rc) return rc;
-  rc = (k == 1 || n / k < c->cfg.base_threshold) ? run_direct(c, P, n, dim) : run_dc(c, P, n, dim, k, frac);
+  if (k == 1 || n / k < c->cfg.base_threshold) rc = run_direct(c, P, n, dim);
+  else if (c->cfg.recursive) rc = run_recursive(c, P, n, dim, k, frac);
+  else rc = run_dc(c, P, n, dim, k, frac);
   if (rc) return rc;
   if (!c->cfg.neighbors && !c->cfg.validate) return 0;
   cudaEventRecord(c->ev[10], c->stream);

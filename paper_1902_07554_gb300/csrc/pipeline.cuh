@@ -13,4 +13,12 @@ void* stage_in(dt_ctx* c, const void* src, size_t bytes, const std::string& name
 int copy_out(dt_ctx* c, void* dst, const void* src, size_t bytes);
 bool is_device_ptr(const void* p);
 __global__ void k_iota(int* a, int64_t n, int start);
+// Base case of Alg. 1: one triangulation of all points (pipeline.cu).
+int run_direct(dt_ctx* c, const void* P, int64_t n, int dim);
+// Recursive bisection (recursive.cu).
+int run_recursive(dt_ctx* c, const void* P, int64_t n, int dim, int k, double frac);
+// Indices i with flag[i] set, ascending; *m receives the count.
+int compact_flags(dt_ctx* c, const unsigned char* flag, int64_t n, int* out, int64_t* m, const char* tag);
+__global__ void k_gather_i32(const int* src, const int* idx, int64_t m, int* out);
+__global__ void k_flag_by_gid(const unsigned char* vflag, const int* gid, int64_t n, unsigned char* fg);
 }  // namespace gdt

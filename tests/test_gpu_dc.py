@@ -26,7 +26,7 @@ def tri():
 
 def _cfg(tri, **kw):
     base = dict(divide=0, primitive=0, weight=0, lp_rounds=16, epsilon=0.05, grid_cell=1.0, seed=1,
-                base_threshold=16, validate=0, cavity_cap=0)
+                base_threshold=16, validate=0, cavity_cap=0, recursive=0, partition_init=0)
     base.update(kw)
     tri.configure(**base)
 
@@ -157,3 +157,54 @@ def test_partition_graph_entry(tri):
             assert np.array_equal(got.astype(np.int64), dv.partition(P[ids], E, w, k, init="hilbert"))
     finally:
         tri.configure(partition_init="auto")
+
+
+@pytest.mark.parametrize("D,n,k,frac,divide", [(2, 20000, 4, 0.01, 0), (2, 20000, 8, 0.01, 1),
+                                               (3, 20000, 8, 0.005, 0), (3, 16000, 4, 0.01, 1)])
+def test_recursive_bisection_matches_oracle(tri, D, n, k, frac, divide):
+    P = pointsets.uniform(n, D, 31) if D == 2 else pointsets.clustered(n, 31)
+    want = oracle.delaunay(P)
+    _cfg(tri, recursive=1, divide=divide, base_threshold=256)
+    got = tri.triangulate(P, k=k, sample_frac=frac).astype(np.int64)
+    st = tri.stats()
+    lab = tri.labels().astype(np.int64)
+    N = tri.neighbors().astype(np.int64)
+    assert np.array_equal(got, want)
+    assert np.array_equal(N, oracle.neighbors(want))
+    assert st.k == k and st.border_vertices > 0 and st.border_dt_simplices > 0
+    ref = dv.recursive_labels(P, k, frac, 1) if divide == 0 else dv.kd_labels(P, k)
+    assert np.array_equal(lab, ref)
+    if divide == 0:   # one fresh sample per node: k - 1 samples
+        L = k.bit_length() - 1
+        eta = sum(dv.sample_size(int(m), frac, D) for t in range(L) for m in np.bincount(lab >> (L - t)) if m)
+        assert st.eta == eta
+
+
+@pytest.mark.parametrize("D,n,k,divide", [(2, 1200, 4, 0), (3, 500, 4, 1)])
+def test_recursive_border_contains_exact_borders(tri, D, n, k, divide):
+    """Per merge the grid border is a superset of the exact one, so the
+    levels' border vertex counts add up to at least the exact counts."""
+    P = pointsets.uniform(n, D, 33)
+    _cfg(tri, recursive=1, divide=divide, base_threshold=16)
+    got = tri.triangulate(P, k=k, sample_frac=0.1).astype(np.int64)
+    st = tri.stats()
+    lab = tri.labels().astype(np.int64)
+    rows, sizes = dv.recursive_merges(P, lab, k)
+    assert np.array_equal(got, rows)
+    assert st.border_vertices >= sum(sum(level) for level in sizes)
+    bv = set(tri.border_vertices().tolist())
+    for h in range(1, k.bit_length()):
+        part = lab >> (h - 1)
+        for v in range(len(sizes[h - 1])):
+            ids = np.nonzero((part >> 1) == v)[0]
+            _, VB, _ = dv.border_exact(P[ids], part[ids] & 1, 2)
+            assert set(ids[VB].tolist()) <= bv
+
+
+def test_recursive_bisection_needs_a_power_of_two(tri):
+    from paper_1902_07554_gb300 import DTError
+    P = pointsets.uniform(5000, 2, 2)
+    _cfg(tri, recursive=1, base_threshold=256)
+    with pytest.raises(DTError, match="ARG"):
+        tri.triangulate(P, k=6)
+    assert np.array_equal(tri.triangulate(P, k=1).astype(np.int64), oracle.delaunay(P))

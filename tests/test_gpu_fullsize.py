@@ -3,7 +3,8 @@ benchmark times.
 
 * 1,000,000 uniform 3D points, k = 16, 0.5 % sample: the whole output is
   compared element by element with the oracle's DT (integer output:
-  bit-exact), for the sample divide and for the kd median divide.
+  bit-exact), for the sample divide, the kd median divide and recursive
+  bisection.
 * 4,000,000 clustered 3D points, k = 64: the full oracle DT takes minutes on
   the host, so the output is certified on the device (local Delaunay, hull
   convexity, Euler characteristic, every point a vertex), must equal the
@@ -41,6 +42,13 @@ def test_uniform3d_1m_k16_matches_oracle(tri):
     finally:
         tri.configure(divide=0)
     assert np.array_equal(kd, want)
+    tri.configure(recursive=1)
+    try:
+        rb = tri.triangulate(P, k=16, sample_frac=0.005).astype(np.int64)
+        assert tri.stats().k == 16
+    finally:
+        tri.configure(recursive=0)
+    assert np.array_equal(rb, want)
 
 
 def _empty_sphere_sample(P, S, m, seed):

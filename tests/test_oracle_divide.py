@@ -180,3 +180,38 @@ def test_degenerate_partition_contributes_all_points(orc):
     Bset, VB, parts = dv.border_exact(P, lab, 3)
     assert set(range(120, 126)) <= set(VB.tolist())
     assert np.array_equal(dv.merge(parts, Bset, VB, P, lab), orc.delaunay(P))
+
+
+def test_recursive_labels_first_level_is_the_direct_bisection():
+    """Depth 0 of recursive bisection is Alg. 2 with k = 2 on all points: the
+    leaves of k = 8 fall on the sides of the k = 2 split."""
+    P = pointsets.uniform(3000, 2, 23)
+    direct = _sample_labels(P, 2, 0.02, 5)
+    assert np.array_equal(dv.recursive_labels(P, 2, 0.02, 5), direct)
+    lab8 = dv.recursive_labels(P, 8, 0.02, 5)
+    assert np.array_equal(lab8 >= 4, direct == 1)
+    sizes = np.bincount(lab8, minlength=8)
+    assert sizes.sum() == 3000 and sizes.min() > 0
+    # the second level splits each half on its own fresh sample
+    left = np.nonzero(direct == 0)[0]
+    eta = dv.sample_size(len(left), 0.02, 2)
+    sids = dv.sample_ids(len(left), eta, 6)
+    E, w = dv.sample_graph(P[left][sids], sids)
+    side = dv.labels(P[left], P[left][sids], sids, dv.partition(P[left][sids], E, w, 2))
+    assert np.array_equal(lab8[left] >= 2, side == 1)
+    with pytest.raises(ValueError):
+        dv.recursive_labels(P, 6, 0.02, 5)
+
+
+@pytest.mark.parametrize("D,n,k,kind", [(2, 600, 4, "sample"), (2, 500, 8, "kd"), (3, 240, 4, "sample"),
+                                        (3, 200, 4, "kd")])
+def test_recursive_merges_reproduce_dt(orc, D, n, k, kind):
+    """k - 1 pairwise merges (Sec. 3.3) reach DT(P), and every node's border is
+    non-empty."""
+    P = pointsets.uniform(n, D, 29) if D == 2 else pointsets.clustered(n, 29)
+    lab = dv.recursive_labels(P, k, 0.1, 4) if kind == "sample" else dv.kd_labels(P, k)
+    rows, sizes = dv.recursive_merges(P, lab, k)
+    assert sum(len(level) for level in sizes) == k - 1
+    assert [len(level) for level in sizes] == [k >> h for h in range(1, k.bit_length())]
+    assert all(x > 0 for level in sizes for x in level)
+    assert np.array_equal(rows, orc.delaunay(P))
