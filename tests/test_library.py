@@ -36,3 +36,25 @@ def test_config_default_and_bad_device():
     assert L.dt_create(ctypes.byref(ctx), 4096, None, None) == -1
     assert L.dt_last_error(None) == b"null context"
     assert L.dt_triangulate(None, None, 0, 2, 1, 0.0) == -1
+
+
+@pytest.mark.parametrize("cname,pyname", [("dt_config", "Config"), ("dt_stats", "Stats"),
+                                          ("dt_validation", "Validation"), ("dt_kernel_profile", "KernelProfile")])
+def test_binding_structs_match_the_header(tmp_path, cname, pyname):
+    """The ctypes mirrors have the header's field names, offsets and size
+    (compiled from include/dt.h with the host C compiler)."""
+    import os
+    cls = getattr(gdt, pyname)
+    fields = [f[0] for f in cls._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dt.h"', 'int main(void) {',
+             f'  printf("%zu\\n", sizeof({cname}));']
+    lines += [f'  printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in fields]
