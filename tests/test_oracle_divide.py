@@ -215,3 +215,14 @@ def test_recursive_merges_reproduce_dt(orc, D, n, k, kind):
     assert [len(level) for level in sizes] == [k >> h for h in range(1, k.bit_length())]
     assert all(x > 0 for level in sizes for x in level)
     assert np.array_equal(rows, orc.delaunay(P))
+
+
+@pytest.mark.parametrize("kind,want", [("log", [511, 223, 1]), ("constant", [1, 1, 1]),
+                                       ("inverse", [1667, 1250, 1000]), ("linear", [400, 200, 1])])
+def test_table1_weights_by_hand(kind, want):
+    """Table 1 on a 3-4-5 triangle: d* = 5 (the box diagonal), so the edges have
+    d = 0.6, 0.8, 1.0; weights are 1000 omega rounded, at least 1 (-ln 0.6 =
+    0.5108, -ln 0.8 = 0.2231, 1/0.6 = 1.6667)."""
+    PS = np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 4.0]])
+    E = np.array([[0, 1], [0, 2], [1, 2]])
+    assert dv.edge_weights(PS, E, kind).tolist() == want
