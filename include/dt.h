@@ -281,6 +281,37 @@ DT_API int dt_get_batch_simplices(dt_ctx* ctx, int32_t* out, int64_t capacity, i
  * DT_E_ARG (fewer than dim+1 points); status: count int32 (host). */
 DT_API int dt_get_batch_status(dt_ctx* ctx, int32_t* status, int count);
 
+/* ---- asynchronous jobs (systems extension; the paper has no counterpart) ---- */
+
+/* Queue one triangulation, exactly what dt_triangulate(points, n, dim, k,
+ * sample_frac) computes, and return at once; *job receives its id (ids start
+ * at 1 and are never reused).  The points (host or device, n x dim float64)
+ * are copied before the call returns; the caller may free them afterwards.
+ * Jobs run in submission order on the context's job worker: a second context
+ * on the same device (created by the first dt_submit with this context's
+ * configuration) with its own stream, buffers and host thread, so they run
+ * alongside this context's own calls.  Argument errors (as dt_triangulate's)
+ * are returned here; errors of the triangulation itself by dt_poll.
+ * Returns DT_OK, DT_E_ARG, DT_E_CUDA or DT_E_NOMEM. */
+DT_API int dt_submit(dt_ctx* ctx, const double* points, int64_t n, int dim, int k, double sample_frac,
+                     uint64_t* job);
+
+/* *done = 1 once the job has finished, else 0.  A finished job returns its
+ * triangulation's result code (DT_OK or the error, with dt_last_error set);
+ * an unknown or released id returns DT_E_ARG. */
+DT_API int dt_poll(dt_ctx* ctx, uint64_t job, int* done);
+
+/* A finished job's simplices, in dt_get_simplices' format (rows of dim+1
+ * sorted global indices, rows sorted); out: HOST memory, capacity rows, NULL
+ * for a size query (*count only).  DT_E_ARG for an unknown or unfinished job;
+ * a failed job returns its error code. */
+DT_API int dt_get_job_simplices(dt_ctx* ctx, uint64_t job, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Frees a finished job's result; DT_E_ARG for an unknown id or a job still
+ * queued or running.  dt_destroy frees every job: it waits for the running
+ * one and drops those still queued. */
+DT_API int dt_release_job(dt_ctx* ctx, uint64_t job);
+
 /* ---- step-level entry points (operate on caller buffers; host or device) ---- */
 
 /* Exact predicate signs for m index tuples into points (n x dim, host or

@@ -133,6 +133,10 @@ def load_library(build: bool = True):
         "dt_select_sample_noalloc": ([i32, p, i64, i64, ctypes.c_uint64, p], i32),
         "dt_get_neighbors": ([p, p, i64, p], i32),
         "dt_validate": ([p, p, i64, i32, p, i64, p], i32),
+        "dt_submit": ([p, p, i64, i32, i32, dbl, p], i32),
+        "dt_poll": ([p, ctypes.c_uint64, p], i32),
+        "dt_get_job_simplices": ([p, ctypes.c_uint64, p, i64, p], i32),
+        "dt_release_job": ([p, ctypes.c_uint64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -177,6 +181,7 @@ class Triangulator:
                 v = INITS[v]
             setattr(cfg, k, v)
         self._cfg = cfg
+        self._job_dim = {}
         rc = self.L.dt_create(ctypes.byref(self.ctx), device, stream, ctypes.byref(cfg))
         if rc:
             raise DTError(rc, "dt_create failed (no CUDA device?)")
@@ -222,6 +227,36 @@ class Triangulator:
         P, n, dim = _as_points(points)
         self._check(self.L.dt_triangulate(self.ctx, _ptr(P), n, dim, k, float(sample_frac)))
         return self.simplices() if fetch else None
+
+    def submit(self, points, k: int = 1, sample_frac: float = 0.0) -> int:
+        """Queue DT(points) on the context's job worker; returns the job id
+        (the points are copied before this returns)."""
+        P, n, dim = _as_points(points)
+        job = ctypes.c_uint64()
+        self._check(self.L.dt_submit(self.ctx, _ptr(P), n, dim, k, float(sample_frac), ctypes.byref(job)))
+        self._job_dim[job.value] = dim
+        return job.value
+
+    def poll(self, job: int) -> bool:
+        """True once the job has finished; raises DTError if it failed."""
+        done = ctypes.c_int()
+        self._check(self.L.dt_poll(self.ctx, job, ctypes.byref(done)))
+        return bool(done.value)
+
+    def job_simplices(self, job: int, release: bool = True):
+        """A finished job's simplices ((m, dim+1) int32, as triangulate
+        returns); the job is released afterwards unless release is False."""
+        cnt = ctypes.c_int64()
+        self._check(self.L.dt_get_job_simplices(self.ctx, job, None, 0, ctypes.byref(cnt)))
+        out = np.empty((cnt.value, self._job_dim[job] + 1), dtype=np.int32)
+        self._check(self.L.dt_get_job_simplices(self.ctx, job, _ptr(out), cnt.value, ctypes.byref(cnt)))
+        if release:
+            self.release_job(job)
+        return out
+
+    def release_job(self, job: int):
+        self._check(self.L.dt_release_job(self.ctx, job))
+        self._job_dim.pop(job, None)
 
     def triangulate_batch(self, points, offsets, fetch: bool = True):
         """Independent DTs of points[offsets[i]:offsets[i+1]]; returns a list of

@@ -7,6 +7,7 @@
 
 #include "ctx.cuh"
 #include "adjacency.cuh"
+#include "jobs.h"
 #include "pipeline.cuh"
 
 using namespace gdt;
@@ -85,6 +86,10 @@ extern "C" int dt_set_config(dt_ctx* c, const dt_config* cfg) {
 
 extern "C" void dt_destroy(dt_ctx* c) {
   if (!c) return;
+  delete c->jobs;            // lets a running job finish, drops queued ones, joins the worker
+  c->jobs = nullptr;
+  if (c->job_ctx) dt_destroy(c->job_ctx);
+  c->job_ctx = nullptr;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   pool_free_all(c);
@@ -515,4 +520,86 @@ extern "C" int dt_eval_predicates(dt_ctx* c, const double* points, int64_t n, in
   if ((int)(hc[1] & 0xffffffff) != (int)(hc[3] & 0xffffffff))
     return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
   return copy_out(c, out, o, m);
+}
+
+// ---------------------------------------------------------------- asynchronous jobs
+// (see include/dt.h)
+extern "C" int dt_submit(dt_ctx* c, const double* points, int64_t n, int dim, int k, double sample_frac,
+                         uint64_t* job) {
+  if (!c) return DT_E_ARG;
+  if (!points || !job || (dim != 2 && dim != 3)) return set_err(c, DT_E_ARG, "points and job must be non-null, dim 2 or 3");
+  if (n < dim + 1 || n >= (int64_t(1) << 28)) return set_err(c, DT_E_ARG, "n must be in [dim+1, 2^28)");
+  if (k < 1 || k > 4096) return set_err(c, DT_E_ARG, "k must be in [1, 4096]");
+  if (!(sample_frac >= 0.0 && sample_frac <= 1.0)) return set_err(c, DT_E_ARG, "sample_frac must be in [0, 1]");
+  if (cudaSetDevice(c->device) != cudaSuccess) { cudaGetLastError(); return set_err(c, DT_E_CUDA, "cudaSetDevice"); }
+  gdt::JobInput in;
+  in.n = n;
+  in.dim = dim;
+  in.k = k;
+  in.frac = sample_frac;
+  in.pts.resize((size_t)n * dim);
+  if (gdt::is_device_ptr(points)) {
+    CUDA_OK(cudaMemcpyAsync(in.pts.data(), points, sizeof(double) * (size_t)n * dim, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(cudaStreamSynchronize(c->stream));
+  } else {
+    memcpy(in.pts.data(), points, sizeof(double) * (size_t)n * dim);
+  }
+  if (!c->jobs) {
+    dt_ctx* w = nullptr;
+    int rc = dt_create(&w, c->device, nullptr, &c->cfg);
+    if (rc) return set_err(c, rc, "job context");
+    c->job_ctx = w;
+    c->jobs = new gdt::JobQueue([w](const gdt::JobInput& j) {
+      gdt::JobResult r;
+      r.rc = dt_triangulate(w, j.pts.data(), j.n, j.dim, j.k, j.frac);
+      int64_t m = 0;
+      if (!r.rc) r.rc = dt_get_simplices(w, nullptr, 0, &m);
+      if (!r.rc) {
+        r.rows.resize((size_t)m * (j.dim + 1));
+        r.rc = dt_get_simplices(w, r.rows.data(), m, &m);
+      }
+      if (r.rc) {
+        r.rows.clear();
+        r.err = dt_last_error(w);
+      }
+      return r;
+    });
+  }
+  *job = c->jobs->submit(std::move(in));
+  return DT_OK;
+}
+
+extern "C" int dt_poll(dt_ctx* c, uint64_t job, int* done) {
+  if (!c) return DT_E_ARG;
+  if (!done) return set_err(c, DT_E_ARG, "done must be non-null");
+  int rc = 0;
+  const int st = c->jobs ? c->jobs->poll(job, &rc) : -1;
+  if (st < 0) return set_err(c, DT_E_ARG, "unknown job");
+  *done = st;
+  if (st && rc) {
+    const gdt::JobResult* r = c->jobs->result(job);
+    return set_err(c, rc, r ? r->err : std::string("job failed"));
+  }
+  return DT_OK;
+}
+
+extern "C" int dt_get_job_simplices(dt_ctx* c, uint64_t job, int32_t* out, int64_t capacity, int64_t* count) {
+  if (!c || !count) return DT_E_ARG;
+  const gdt::JobResult* r = c->jobs ? c->jobs->result(job) : nullptr;
+  if (!r) return set_err(c, DT_E_ARG, "unknown or unfinished job");
+  if (r->rc) return set_err(c, r->rc, r->err);
+  const int64_t ints = (int64_t)r->rows.size();
+  *count = r->dim ? ints / (r->dim + 1) : 0;
+  if (!out) return DT_OK;
+  if (capacity < *count) return set_err(c, DT_E_ARG, "capacity too small");
+  if (ints) memcpy(out, r->rows.data(), sizeof(int32_t) * (size_t)ints);
+  return DT_OK;
+}
+
+extern "C" int dt_release_job(dt_ctx* c, uint64_t job) {
+  if (!c) return DT_E_ARG;
+  const int st = c->jobs ? c->jobs->release(job) : -1;
+  if (st < 0) return set_err(c, DT_E_ARG, "unknown job");
+  if (st == 0) return set_err(c, DT_E_ARG, "job still queued or running");
+  return DT_OK;
 }

@@ -7,6 +7,8 @@
 #include "common.cuh"
 #include "engine.cuh"
 
+namespace gdt { class JobQueue; }
+
 struct dt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -53,6 +55,9 @@ struct dt_ctx {
   std::vector<int64_t> batch_offsets;
   std::vector<int> batch_status;
   int batch_count = 0;
+  // asynchronous jobs (dt_submit): a second context on the same device and its worker
+  dt_ctx* job_ctx = nullptr;
+  gdt::JobQueue* jobs = nullptr;
 };
 
 namespace gdt {
