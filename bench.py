@@ -77,6 +77,10 @@ def gen_points(w, seed_offset=0):
     return pointsets.clustered(w["n"], w["seed"] + seed_offset)
 
 
+# FP32 FMA rate of one GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.070 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
 def cavity_fingerprint() -> str:
     """SHA-1 of the source of the dominant kernel (region growth + k_cavity_w):
     a stored DRAM-traffic figure only applies to the kernel it was taken on."""
@@ -481,6 +485,14 @@ def main():
                     "filter_gflops": a["flops"] / (a["ms"] / 1e3) / 1e9 if a["ms"] > 0 else 0.0,
                     "launches": a["launches"], "ms_per_launch": per_launch_ms,
                     "bytes_per_launch": bytes_per_launch}
+        # second roof of the same kernel: the conflict-test arithmetic (FP32 first stage)
+        # against the FP32 rate derived from the unit counts and the maximum SM clock
+        fp32_tflops = FP32_PEAK_TFLOPS
+        filt = roofline["filter_gflops"] / 1e3
+        roofline["alu"] = {"bound": "alu", "achieved": filt, "peak": fp32_tflops, "unit": "TFLOP/s",
+                           "frac": filt / fp32_tflops,
+                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                           "work": "220 flops per 3D conflict test (70 in 2D), counted per test on the device"}
     kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in prof_tot.items()}
 
     cpu = None
