@@ -182,7 +182,67 @@ def cpu_baseline(w, budget_s: float = 15.0):
         dt = time.perf_counter() - t
         m = m2
     return {"value": m / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {m} of the {w['n']} workload points, one full DT by the C oracle, {dt:.2f} s"}
+            "sample": f"first {m} of the {w['n']} workload points, one full DT by the C oracle, {dt:.2f} s",
+            "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (or its architecture when /proc does not say)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_batch_chunk(job):
+    """Worker of the all-core oracle baseline: generates and triangulates the
+    batch instances it is given; returns their point count."""
+    import oracle
+    ids, count, seed = job
+    pts = 0
+    for i in ids:
+        Q = pointsets.batch_instance(i, count=count, seed=seed)
+        oracle.delaunay(Q)
+        pts += len(Q)
+    return pts
+
+
+def cpu_baseline_batch(P, off, seed: int, budget_s: float = 8.0):
+    """The CPU oracle on the batch workload's first instances: one core
+    (instances in order for about budget_s), then every host core (a spawn
+    pool started and warmed before the clock; each process generates and
+    triangulates its share of as many instances per core)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import oracle
+    count = len(off) - 1
+    t0 = time.perf_counter()
+    i = 0
+    while i < count and (i == 0 or time.perf_counter() - t0 < budget_s):
+        oracle.delaunay(P[off[i]:off[i + 1]])
+        i += 1
+    dt1 = time.perf_counter() - t0
+    pts1 = int(off[i] - off[0])
+    cores = os.cpu_count() or 1
+    m = min(count, i * cores)
+    shares = [(list(range(c, m, cores)), count, seed) for c in range(cores)]
+    with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_batch_chunk, [([0], count, seed)] * cores))   # start and warm the processes
+        t0 = time.perf_counter()
+        ptsn = sum(ex.map(_oracle_batch_chunk, shares))
+        dtn = time.perf_counter() - t0
+    return {"value": pts1 / dt1 / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {i} of the {count} instances ({pts1} points), one full DT each by the C oracle, "
+                      f"one core, {dt1:.2f} s",
+            "all_cores": {"value": ptsn / dtn / 1e6, "unit": "Mpoints/s", "cores": cores,
+                          "sample": f"first {m} instances ({ptsn} points) spread over {cores} processes, {dtn:.2f} s"},
+            "cpu_model": cpu_model()}
 
 
 def run_reference(args, w):
@@ -257,6 +317,7 @@ def run_batch(args, w):
         e2e.append(time.perf_counter() - t)
     nout = sum(len(r) for r in res)
     st = tri.stats()
+    cpu = None if args.no_cpu_baseline else cpu_baseline_batch(P, off, w["seed"])
     line = {"metric": METRIC, "value": n / (ms / 1e3) / 1e6, "unit": "Mpoints/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -264,7 +325,7 @@ def run_batch(args, w):
                        "l2": "flushed before every step (256 MiB write)"},
             "e2e": {"value": n / (sum(e2e) / len(e2e)) / 1e6, "unit": "Mpoints/s",
                     "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": nout * 12},
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu,
             "stats": {"simplices": nout, "rounds_max": st.rounds_max}}
     print(json.dumps(line), flush=True)
     return 0

@@ -142,6 +142,19 @@ def batch_instances(count: int = 4096, seed: int = 4, lo: int = 256, hi: int = 6
     return pts, offsets, kinds
 
 
+def batch_instance(i: int, count: int = 4096, seed: int = 4, lo: int = 256, hi: int = 65536,
+                   dim: int = 2) -> np.ndarray:
+    """Instance i of batch_instances(count, seed, lo, hi, dim) alone (the same
+    points, without generating the others)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), size=count))).astype(np.int64)
+    m = int(np.clip(sizes, lo, hi)[i])
+    r = np.random.default_rng(seed + 1 + i)
+    if r.random() < 0.5:
+        return r.random((m, dim))
+    return r.normal(0.5, 0.1, size=(m, dim))
+
+
 def serve_jobs(count: int, seed: int = 5, lo: int = 1000, hi: int = 2_000_000):
     """Job sizes log-uniform in [lo, hi] and a kind per job (uniform or
     clustered).  Arrival times are drawn by the serving driver from the offered
