@@ -245,6 +245,25 @@ def cpu_baseline_batch(P, off, seed: int, budget_s: float = 8.0):
             "cpu_model": cpu_model()}
 
 
+def cpu_baseline_jobs(pts, budget_s: float = 8.0):
+    """The CPU oracle on the serving workload's first jobs, one core, in order
+    for about budget_s (at least one job; every job is cut to its first
+    100,000 points)."""
+    import oracle
+    t0 = time.perf_counter()
+    done, npts = 0, 0
+    while done < len(pts) and (done == 0 or time.perf_counter() - t0 < budget_s):
+        Q = pts[done][:100_000]
+        oracle.delaunay(Q)
+        npts += len(Q)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": npts / dt / 1e6, "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of the {len(pts)} jobs ({npts} points; jobs cut to 100,000 points), "
+                      f"one full DT each by the C oracle, {dt:.2f} s",
+            "host_cores": os.cpu_count(), "cpu_model": cpu_model()}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -376,12 +395,14 @@ def run_serving(args, w):
     clk.start()
     served = srv.run(jobs)
     clocks = clk.stop()
+    cpu = None if args.no_cpu_baseline else cpu_baseline_jobs(pts)
     line = {"metric": METRIC, "value": served["throughput_mpts"], "unit": "Mpoints/s", "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": served["makespan_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "jobs": len(pts), "points": total, "offered_load": w["load"],
                        "budget_gb": 120, "workers": 3},
             "serve": {"served": served, "plain": plain_sum}, "clocks": clocks, "gpu_launches": served["launches"],
+            "cpu_baseline": cpu,
             "e2e": {"value": served["throughput_mpts"], "unit": "Mpoints/s",
                     "h2d_bytes_per_step": total * 24, "d2h_bytes_per_step": int(served["rows_out"]) * 16}}
     print(json.dumps(line), flush=True)
