@@ -107,7 +107,7 @@ typedef struct dt_config {
   int brio_drain;        /* the next BRIO batch is activated when the active set has drained to
                             1 / brio_drain of the last batch; 0 = automatic (8) */
   int partition_init;    /* DT_INIT_*: initial blocks of the sample partitioner */
-  int recursive;         /* 1: recursive bisection (Sec. 3.3): the divide applied log2 k times with
+  int recursive;         /* 1: recursive bisection (Sec. 3.1): the divide applied log2 k times with
                             k' = 2 (a fresh sample per node, or the kd median split) and k - 1 merges,
                             batched level by level; k must be a power of two */
 } dt_config;

@@ -258,7 +258,7 @@ def kd_labels(P: np.ndarray, k: int) -> np.ndarray:
 # ---------------------------------------------------------------- recursive bisection
 def recursive_labels(P: np.ndarray, k: int, frac: float, seed: int, eps: float = 0.05, rounds: int = 16,
                      init: str = "kd", weight: str = "log") -> np.ndarray:
-    """Recursive bisection with the sample divide (Sec. 3.3): Alg. 2 applied
+    """Recursive bisection with the sample divide (Sec. 3.1): Alg. 2 applied
     log2 k times with k' = 2.  A node is named by its first leaf; it holds the
     points labelled with that leaf, in ascending global index, and its local
     index of a point is the point's rank there.  At depth t every node with kk
@@ -291,7 +291,7 @@ def recursive_labels(P: np.ndarray, k: int, frac: float, seed: int, eps: float =
 
 
 def recursive_merges(P: np.ndarray, lab: np.ndarray, k: int):
-    """The k - 1 merges of recursive bisection, bottom-up (Sec. 3.3): at level
+    """The k - 1 merges of recursive bisection, bottom-up (Sec. 3.1): at level
     h (1..log2 k) the parts are the leaves with the h - 1 low bits dropped, and
     node v merges parts 2v and 2v + 1 by Alg. 1 with k = 2 on its own points
     (exact border, border triangulation, merge rule).  Returns the merged

@@ -1,4 +1,4 @@
-// recursive.cu -- recursive bisection (Sec. 3.3, "Recursive Bisection &
+// recursive.cu -- recursive bisection (Sec. 3.1, "Recursive Bisection &
 // Direct k-way Partitioning"): the divide is applied log2 k times with
 // k' = 2 -- every node draws a fresh sample of its own points, triangulates
 // and bisects it and assigns its points (Alg. 2), or splits at the median of

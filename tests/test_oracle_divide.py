@@ -206,7 +206,7 @@ def test_recursive_labels_first_level_is_the_direct_bisection():
 @pytest.mark.parametrize("D,n,k,kind", [(2, 600, 4, "sample"), (2, 500, 8, "kd"), (3, 240, 4, "sample"),
                                         (3, 200, 4, "kd")])
 def test_recursive_merges_reproduce_dt(orc, D, n, k, kind):
-    """k - 1 pairwise merges (Sec. 3.3) reach DT(P), and every node's border is
+    """k - 1 pairwise merges (Sec. 3.1) reach DT(P), and every node's border is
     non-empty."""
     P = pointsets.uniform(n, D, 29) if D == 2 else pointsets.clustered(n, 29)
     lab = dv.recursive_labels(P, k, 0.1, 4) if kind == "sample" else dv.kd_labels(P, k)
