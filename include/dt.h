@@ -85,7 +85,7 @@ extern "C" {
 typedef struct dt_config {
   int divide;            /* DT_DIVIDE_*; default DT_DIVIDE_SAMPLE */
   int primitive;         /* DT_PRIM_*; default DT_PRIM_GRID */
-  int weight;            /* DT_WEIGHT_*; default DT_WEIGHT_LOG (Sec. 4.3) */
+  int weight;            /* DT_WEIGHT_*; default DT_WEIGHT_LOG (Sec. 4.4) */
   int lp_rounds;         /* label-propagation rounds of the partitioner; default 16 */
   double epsilon;        /* partition imbalance, |V_i| <= (1+eps) ceil(|V|/k); default 0.05 */
   double grid_cell;      /* c_G: grid cell edge in units of the mean point spacing; default 1 */
@@ -189,7 +189,7 @@ DT_API int dt_set_config(dt_ctx* ctx, const dt_config* cfg);
 /* Triangulate n points of dimension dim (2 or 3), points host or device,
  * with k partitions (k >= 1; k = 1 triangulates directly) and sample
  * fraction sample_frac in [0, 1] (0 selects the paper's default
- * eta = ceil(sqrt(n)), Sec. 4.1).  Device points must stay valid until the
+ * eta = ceil(sqrt(n)), Sec. 4.2).  Device points must stay valid until the
  * call returns.  The result replaces the context's previous result.
  * Errors: DT_E_ARG, DT_E_DUPLICATE, DT_E_DEGENERATE, DT_E_NOMEM,
  * DT_E_TIMEOUT, DT_E_OVERFLOW, DT_E_RANGE, DT_E_CUDA, DT_E_INTERNAL. */

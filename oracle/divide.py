@@ -29,7 +29,7 @@ def splitmix64(x: int) -> int:
 
 def sample_size(n: int, frac: float, D: int) -> int:
     """eta(n): ceil(frac * n), or ceil(sqrt(n)) when frac == 0 (the paper's
-    default, Sec. 4.1); at least D + 2 and at most n."""
+    default, Sec. 4.2); at least D + 2 and at most n."""
     eta = math.ceil(math.sqrt(n)) if frac <= 0 else math.ceil(frac * n)
     return int(min(n, max(D + 2, eta)))
 
