@@ -226,3 +226,14 @@ def test_table1_weights_by_hand(kind, want):
     PS = np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 4.0]])
     E = np.array([[0, 1], [0, 2], [1, 2]])
     assert dv.edge_weights(PS, E, kind).tolist() == want
+
+
+@pytest.mark.parametrize("shape,k", [((24, 20), 4), ((8, 7, 6), 2)])
+def test_recursive_merges_on_a_lattice(orc, shape, k):
+    """Maximally degenerate input (cocircular / cospherical lattice points):
+    the perturbed predicates keep the k - 1 merges exact."""
+    P = pointsets.grid(shape, seed=3)
+    lab = dv.kd_labels(P, k)
+    rows, sizes = dv.recursive_merges(P, lab, k)
+    assert np.array_equal(rows, orc.delaunay(P))
+    assert sum(len(level) for level in sizes) == k - 1
