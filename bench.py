@@ -309,6 +309,11 @@ def run_batch(args, w):
     P_dev = torch.from_numpy(P).to(f"cuda:{local}")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     torch.cuda.synchronize()
+    schedule = None
+    if args.autotune:                      # untimed: picks the schedule the timed steps use
+        from paper_1902_07554_gb300 import tune
+        r = tune.autotune(tri, P_dev, offsets=off, reps=1)
+        schedule = {"best": r["best"], "ms": r["ms"], "candidates": len(r["table"])}
     for _ in range(args.warmup):
         tri.L.dt_triangulate_batch(tri.ctx, ctypes_ptr(P_dev), ctypes_ptr(off), len(off) - 1, 2)
     clk = ClockSampler(local)
@@ -341,7 +346,8 @@ def run_batch(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "instances": len(off) - 1, "points": n, "dim": 2,
-                       "l2": "flushed before every step (256 MiB write)"},
+                       "l2": "flushed before every step (256 MiB write)",
+                       "schedule": schedule or "default (brio_growth 150, brio_drain 8, first_batch 32)"},
             "e2e": {"value": n / (sum(e2e) / len(e2e)) / 1e6, "unit": "Mpoints/s",
                     "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": nout * 12},
             "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu,
@@ -417,6 +423,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform3d_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--divide", default="sample", choices=["sample", "kd"])
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the candidate insertion schedules on the workload first and use the fastest")
     ap.add_argument("--recursive", action="store_true",
                     help="recursive bisection (log2 k bisections, k - 1 merges) instead of direct k-way")
     ap.add_argument("--no-cpu-baseline", action="store_true")
