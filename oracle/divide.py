@@ -338,6 +338,27 @@ def partial_triangulations(P: np.ndarray, lab: np.ndarray, k: int):
     return out
 
 
+def _is_border(P: np.ndarray, ids: np.ndarray, row: np.ndarray, others: np.ndarray) -> bool:
+    """The exact test of one simplex of T_i (raw mesh row, local ids, -1 = the
+    infinite vertex) against the points of the other partitions: a finite
+    simplex is a border simplex iff its perturbed circumsphere contains one of
+    them; a ghost (hull facet f) iff one of them is in conflict with it
+    (strictly beyond f, or on f's hyperplane and inside f's circumsphere)."""
+    if (row == -1).any():
+        g = int(np.nonzero(row == -1)[0][0])
+        fin = ids[row[row >= 0]]
+        for q in others:
+            tup = [int(ids[x]) if x >= 0 else -1 for x in row]
+            tup[g] = int(q)
+            o = predicates(P, "orient", np.array([tup], dtype=np.int32))[0]
+            if o > 0 or (o == 0 and _coplanar_conflict(P, fin, q)):
+                return True
+        return False
+    s = ids[row]
+    tup = np.concatenate([np.repeat(s[None, :], len(others), axis=0), others[:, None]], axis=1).astype(np.int32)
+    return bool(np.any(predicates(P, "insphere", tup) > 0))
+
+
 def border_exact(P: np.ndarray, lab: np.ndarray, k: int):
     """Alg. 1 (border detection) with the exact primitive and every simplex tested
     (a superset of what a breadth-first search from the hull reaches).
@@ -360,30 +381,50 @@ def border_exact(P: np.ndarray, lab: np.ndarray, k: int):
         others = np.nonzero(lab != i)[0]
         # all points, global indexing; test every simplex of the raw mesh
         for row in v:
-            if (row == -1).any():
-                g = int(np.nonzero(row == -1)[0][0])
-                fin = ids[row[row >= 0]]
-                hit = False
-                for q in others:
-                    tup = [int(ids[x]) if x >= 0 else -1 for x in row]
-                    tup[g] = int(q)
-                    o = predicates(P, "orient", np.array([tup], dtype=np.int32))[0]
-                    if o > 0:
-                        hit = True
-                        break
-                    if o == 0 and _coplanar_conflict(P, fin, q):
-                        hit = True
-                        break
-                if hit:
-                    VB.update(int(x) for x in fin)
-            else:
-                s = ids[row]
-                tup = np.concatenate([np.repeat(s[None, :], len(others), axis=0),
-                                      others[:, None]], axis=1).astype(np.int32)
-                r = predicates(P, "insphere", tup)
-                if np.any(r > 0):
-                    Bset.add(tuple(sorted(int(x) for x in s)))
-                    VB.update(int(x) for x in s)
+            if not _is_border(P, ids, row, others):
+                continue
+            fin = [int(ids[x]) for x in row if x >= 0]
+            VB.update(fin)
+            if len(fin) == D + 1:
+                Bset.add(tuple(sorted(fin)))
+    return Bset, np.array(sorted(VB), dtype=np.int64), parts
+
+
+def border_exact_bfs(P: np.ndarray, lab: np.ndarray, k: int):
+    """Alg. 1 (border detection) as the paper words it: per partition, a
+    breadth-first search seeded with the simplices on the convex hull of T_i
+    (its ghosts and the finite simplices next to them) that grows only
+    through border simplices, each tested exactly as in border_exact.
+    Returns (border finite simplices, sorted vertices(B), parts) like
+    border_exact; its set is a subset of border_exact's."""
+    from collections import deque
+    n, D = P.shape
+    parts = partial_triangulations(P, lab, k)
+    Bset = set()
+    VB = set()
+    for i, (ids, T, _) in enumerate(parts):
+        if T is None:
+            VB.update(int(x) for x in ids)
+            continue
+        _, v, nb = delaunay(P[ids], ids, mesh=True)
+        others = np.nonzero(lab != i)[0]
+        ghost = (v == -1).any(axis=1)
+        seeds = {int(s) for s in np.nonzero(ghost)[0]}
+        seeds |= {int(x) for s in np.nonzero(ghost)[0] for x in nb[s] if x >= 0 and not ghost[x]}
+        queue = deque(sorted(seeds))
+        seen = set(seeds)
+        while queue:
+            s = queue.popleft()
+            if not _is_border(P, ids, v[s], others):
+                continue
+            fin = [int(ids[x]) for x in v[s] if x >= 0]
+            VB.update(fin)
+            if len(fin) == D + 1:
+                Bset.add(tuple(sorted(fin)))
+            for x in nb[s]:
+                if x >= 0 and int(x) not in seen:
+                    seen.add(int(x))
+                    queue.append(int(x))
     return Bset, np.array(sorted(VB), dtype=np.int64), parts
 
 

@@ -237,3 +237,29 @@ def test_recursive_merges_on_a_lattice(orc, shape, k):
     rows, sizes = dv.recursive_merges(P, lab, k)
     assert np.array_equal(rows, orc.delaunay(P))
     assert sum(len(level) for level in sizes) == k - 1
+
+
+def test_bfs_border_equals_the_sweep_on_connected_partitions():
+    """Alg. 1's hull-seeded breadth-first search reaches the same exact border
+    set as testing every simplex when the partitions have no islands."""
+    P = pointsets.uniform(1500, 2, 1)
+    lab = _sample_labels(P, 4, 0.05, 1)
+    B1, V1, _ = dv.border_exact(P, lab, 4)
+    B2, V2, _ = dv.border_exact_bfs(P, lab, 4)
+    assert B1 == B2 and np.array_equal(V1, V2)
+
+
+def test_bfs_border_misses_an_island(orc):
+    """A partition enclosed by another (an island, which unions of Voronoi
+    cells allow): the simplices of the outer partition that span the island
+    are border simplices unreachable from its hull, so the breadth-first
+    search misses them and the merge is wrong; testing every simplex (the
+    GPU's sweep) keeps it exact."""
+    P = pointsets.uniform(800, 2, 11)
+    lab = (np.linalg.norm(P - 0.5, axis=1) < 0.15).astype(np.int64)
+    want = orc.delaunay(P)
+    B1, V1, parts = dv.border_exact(P, lab, 2)
+    B2, V2, _ = dv.border_exact_bfs(P, lab, 2)
+    assert B2 < B1
+    assert np.array_equal(dv.merge(parts, B1, V1, P, lab), want)
+    assert not np.array_equal(dv.merge(parts, B2, V2, P, lab), want)
