@@ -81,6 +81,43 @@ def gen_points(w, seed_offset=0):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def make_roofline(prof_tot: dict, prof_step_ms: list, n: int, steps: int, peaks: dict, peak_src: str):
+    """Roofline of the kernel with the largest total time in the profiled
+    steps (prof_tot: name -> {"ms", "launches", "bytes", "flops"} summed over
+    `steps` steps; prof_step_ms: each profiled step's time).  achieved =
+    algorithmic bytes per launch / mean launch time, against the HBM peak;
+    traffic = the stored ncu DRAM bytes per point scaled to one launch (when
+    taken on the current kernel source); `alu` = the same kernel's
+    conflict-test arithmetic against the derived FP32 rate."""
+    dom = max(prof_tot.items(), key=lambda kv: kv[1]["ms"]) if prof_tot else None
+    if not dom:
+        return None
+    name, a = dom
+    per_launch_ms = a["ms"] / max(a["launches"], 1)
+    bytes_per_launch = a["bytes"] / max(a["launches"], 1)
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    bpp = stored_cavity_traffic() if name == "k_cavity_w<3>" else None
+    traffic = bpp * n / max(a["launches"] / max(steps, 1), 1) if bpp else None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "traffic_source": ("ncu DRAM bytes on uniform3d_200k (host-driven rounds) scaled by points; "
+                                   "profiles/k_cavity_w_traffic.md") if traffic else None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "share_of_step": a["ms"] / sum(prof_step_ms) if sum(prof_step_ms) > 0 else None,
+                "timing": "CUDA events around every launch, K profiled steps after the timed region",
+                "filter_gflops": a["flops"] / (a["ms"] / 1e3) / 1e9 if a["ms"] > 0 else 0.0,
+                "launches": a["launches"], "ms_per_launch": per_launch_ms,
+                "bytes_per_launch": bytes_per_launch}
+    # second roof of the same kernel: the conflict-test arithmetic (FP32 first stage)
+    # against the FP32 rate derived from the unit counts and the maximum SM clock
+    filt = roofline["filter_gflops"] / 1e3
+    roofline["alu"] = {"bound": "alu", "achieved": filt, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": filt / FP32_PEAK_TFLOPS,
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                       "work": "220 flops per 3D conflict test (70 in 2D), counted per test on the device"}
+    return roofline
+
+
 def cavity_fingerprint() -> str:
     """SHA-1 of the source of the dominant kernel (region growth + k_cavity_w):
     a stored DRAM-traffic figure only applies to the kernel it was taken on."""
@@ -556,33 +593,7 @@ def main():
 
     # ---------------- roofline of the dominant kernel (live CUDA-event times)
     peaks, peak_src = load_peaks()
-    dom = max(prof_tot.items(), key=lambda kv: kv[1]["ms"]) if prof_tot else None
-    roofline = None
-    if dom:
-        name, a = dom
-        per_launch_ms = a["ms"] / max(a["launches"], 1)
-        bytes_per_launch = a["bytes"] / max(a["launches"], 1)
-        achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
-        bpp = stored_cavity_traffic() if name == "k_cavity_w<3>" else None
-        traffic = bpp * n / max(a["launches"] / max(args.steps, 1), 1) if bpp else None
-        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    "traffic_source": ("ncu DRAM bytes on uniform3d_200k (host-driven rounds) scaled by points; "
-                                       "profiles/k_cavity_w_traffic.md") if traffic else None,
-                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-                    "share_of_step": a["ms"] / sum(prof_step_ms),
-                    "timing": "CUDA events around every launch, K profiled steps after the timed region",
-                    "filter_gflops": a["flops"] / (a["ms"] / 1e3) / 1e9 if a["ms"] > 0 else 0.0,
-                    "launches": a["launches"], "ms_per_launch": per_launch_ms,
-                    "bytes_per_launch": bytes_per_launch}
-        # second roof of the same kernel: the conflict-test arithmetic (FP32 first stage)
-        # against the FP32 rate derived from the unit counts and the maximum SM clock
-        fp32_tflops = FP32_PEAK_TFLOPS
-        filt = roofline["filter_gflops"] / 1e3
-        roofline["alu"] = {"bound": "alu", "achieved": filt, "peak": fp32_tflops, "unit": "TFLOP/s",
-                           "frac": filt / fp32_tflops,
-                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                           "work": "220 flops per 3D conflict test (70 in 2D), counted per test on the device"}
+    roofline = make_roofline(prof_tot, prof_step_ms, n, args.steps, peaks, peak_src)
     kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in prof_tot.items()}
 
     cpu = None

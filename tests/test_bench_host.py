@@ -40,3 +40,23 @@ def test_stored_traffic_only_for_the_kernel_it_was_taken_on(monkeypatch):
 
 def test_derived_fp32_roof():
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.07e-3)
+
+
+def test_roofline_from_profiled_kernel_times():
+    """The dominant kernel's roofline from per-kernel totals over K profiled
+    steps (the figures of a measured 1M-point run)."""
+    launches = 3787
+    prof = {"k_cavity_w<3>": {"ms": 319.261, "launches": launches, "bytes": 36927271.45814629 * launches,
+                              "flops": 487.258486271189e9 * 0.319261},
+            "k_insert_w<3>": {"ms": 103.117, "launches": launches, "bytes": 0.0, "flops": 0.0}}
+    r = bench.make_roofline(prof, [150.0] * 5, 1_000_000, 5, {"hbm_gbs": 6800.7}, "measured")
+    assert r["kernel"] == "k_cavity_w<3>" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(438.02, rel=1e-4)
+    assert r["frac"] == pytest.approx(438.02 / 6800.7, rel=1e-4)
+    assert r["share_of_step"] == pytest.approx(319.261 / 750.0)
+    assert r["alu"]["achieved"] == pytest.approx(0.48726, rel=1e-4)
+    assert r["alu"]["frac"] == pytest.approx(0.48726 / bench.FP32_PEAK_TFLOPS, rel=1e-4)
+    stored = bench.stored_cavity_traffic()
+    if stored is not None:   # DRAM bytes per point scaled to one launch (launches per step = 3787 / 5)
+        assert r["traffic"] == pytest.approx(stored * 1_000_000 / (launches / 5))
+    assert bench.make_roofline({}, [], 1, 1, {"hbm_gbs": 1.0}, "fallback") is None
