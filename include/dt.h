@@ -250,6 +250,14 @@ DT_API int dt_get_border_vertices(dt_ctx* ctx, int32_t* out, int64_t capacity, i
  * number available in *count. */
 DT_API int dt_get_kernel_profile(dt_ctx* ctx, dt_kernel_profile* out, int max, int* count);
 
+/* Measured arithmetic roof of the predicate stages: the FMA throughput of
+ * the GPU's FP32 (precision 32) or FP64 (precision 64) pipe, in TFLOP/s
+ * (2 flops per FMA), the best of `reps` timed launches (1..1000) after one
+ * untimed launch of independent FMA chains on every SM.  Needs no context;
+ * the caller's current device is unchanged.  Returns DT_OK, DT_E_ARG or
+ * DT_E_CUDA. */
+DT_API int dt_measure_fma_rate(int device, int precision, int reps, double* tflops);
+
 /* Human-readable description of the last error on this context (never NULL). */
 DT_API const char* dt_last_error(dt_ctx* ctx);
 
@@ -350,7 +358,9 @@ DT_API int dt_partition_graph(dt_ctx* ctx, const double* S, int64_t eta, int dim
  * Needs no context and allocates nothing: its scratch is one file-scope
  * device array of 9240 bytes that every GPU loading this library keeps until
  * the process exits.  out_ids: eta int32 in DEVICE memory of `device`
- * (caller-allocated; host pointers are rejected), written in ascending order.
+ * (caller-allocated; host pointers and memory of another GPU are rejected
+ * with DT_E_ARG before anything runs), written in ascending order.  The
+ * caller's current device is the same after the call as before it.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream); the call
  * synchronises it before returning.
  * Limits: 1 <= eta <= n <= 2^31 - 1; anything else returns DT_E_ARG.

@@ -121,6 +121,15 @@ __global__ void k_na_write(long long n, long long chunk, unsigned long long s, c
 
 static std::mutex g_na_mu;
 static void* g_na_addr[64];
+static int g_na_sms[64];
+
+// Restores the caller's current device on every return path: the call has
+// no context of its own, so it must not leave `device` current behind it.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() { if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; } }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
 
 }  // namespace gdt
 
@@ -132,11 +141,14 @@ extern "C" int dt_select_sample_noalloc(int device, void* cuda_stream, int64_t n
   if (n < 1 || n > 0x7fffffffLL || eta < 1 || eta > n) return DT_E_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) { cudaGetLastError(); return DT_E_ARG; }
-  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return DT_E_CUDA; }
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, out_ids) != cudaSuccess) { cudaGetLastError(); return DT_E_ARG; }
   if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return DT_E_ARG;   // needs device memory
+  if (a.type == cudaMemoryTypeDevice && a.device != device) return DT_E_ARG;                 // of this device
+  DeviceGuard guard;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return DT_E_CUDA; }
   NoAllocScratch* S = nullptr;
+  int sms = 0;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_addr[device]) {
@@ -145,14 +157,22 @@ extern "C" int dt_select_sample_noalloc(int device, void* cuda_stream, int64_t n
         cudaGetLastError();
         return DT_E_CUDA;
       }
+      int m = 0;
+      if (cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || m < 1) {
+        cudaGetLastError();
+        return DT_E_CUDA;
+      }
+      g_na_sms[device] = m;
       g_na_addr[device] = p;
     }
     S = (NoAllocScratch*)g_na_addr[device];
+    sms = g_na_sms[device];
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   unsigned long long sm = splitmix64(seed);
   k_na_reset<<<1, 256, 0, s>>>(S, (long long)eta);
-  unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 152 * 8);
+  // histogram passes: at most 8 blocks of 256 threads per SM (grid-stride loop)
+  unsigned g = (unsigned)std::min<long long>((n + 255) / 256, (long long)sms * 8);
   for (int shift = 56; shift >= 0; shift -= 8) {
     k_na_hist<<<g, 256, 0, s>>>((long long)n, sm, S, shift);
     k_na_pick<<<1, 1, 0, s>>>(S, shift);

@@ -53,3 +53,19 @@ def test_noalloc_rejects_bad_sizes():
     assert L.dt_select_sample_noalloc(0, None, 1 << 31, 8, ctypes.c_uint64(1), ptr) == -1
     host = np.empty(8, dtype=np.int32)
     assert L.dt_select_sample_noalloc(0, None, 100, 8, ctypes.c_uint64(1), ctypes.c_void_p(host.ctypes.data)) == -1
+
+
+def test_noalloc_rejects_memory_of_another_gpu():
+    """An output buffer on a GPU other than the one named in the call is
+    rejected before any kernel is launched (it would be a peer write)."""
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    from paper_1902_07554_gb300 import load_library
+    L = load_library()
+    out = torch.full((8,), -1, dtype=torch.int32, device="cuda:1")
+    torch.cuda.synchronize(1)
+    cur = torch.cuda.current_device()
+    assert L.dt_select_sample_noalloc(0, None, 100, 8, ctypes.c_uint64(1), ctypes.c_void_p(out.data_ptr())) == -1
+    assert torch.cuda.current_device() == cur
+    assert torch.all(out.cpu() == -1)
