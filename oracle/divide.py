@@ -146,45 +146,54 @@ def partition_bounds(eta: int, k: int, eps: float):
     return lmin, lmax
 
 
-def partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float = 0.05,
-              rounds: int = 16, init: str = "kd") -> np.ndarray:
-    """Size-constrained k-way partition of the sample graph (stands in for
-    KaHIP, which is not available).  Deterministic:
-
-    1. initial blocks: with init "hilbert", sample vertices in Hilbert order
-       (ties: vertex index) cut into k consecutive runs,
-       block = floor(rank * k / eta); with init "kd", the kd median split of
-       the sample points (`kd_labels`, ties: vertex index);
-    2. `rounds` rounds of synchronous label propagation.  In round r only
-       vertices with v % 2 == r % 2 move.  A vertex's target is the
-       neighbouring block with the largest total edge weight to it (ties:
-       smaller block), if that beats its own block.  Candidates are taken in
-       vertex order: the j-th candidate into block b is accepted if
-       j < Lmax - |V_b| and, as the j'-th candidate leaving its block a,
-       j' < |V_a| - Lmin.
-    """
-    eta, D = PS.shape
-    if k <= 1:
-        return np.zeros(eta, dtype=np.int64)
-    if init == "kd":
-        block = kd_labels(PS, k)
-    else:
-        bits = hilbert_bits(D)
-        q = quantize(PS, bits)
-        keys = np.array([hilbert_key(q[i], bits) for i in range(eta)], dtype=np.int64)
-        order = np.lexsort((np.arange(eta), keys))
-        block = np.empty(eta, dtype=np.int64)
-        block[order] = (np.arange(eta) * k) // eta
-    lmin, lmax = partition_bounds(eta, k, eps)
-    # adjacency lists with weights
-    nbrs = [[] for _ in range(eta)]
+def adjacency(n: int, E: np.ndarray, w: np.ndarray):
+    """Neighbour lists of the graph (E: rows u < v, w: integer weights):
+    nbrs[v] = [(u, w(v, u)), ...] sorted by u."""
+    nbrs = [[] for _ in range(n)]
     for (u, v), ww in zip(E, w):
-        nbrs[u].append((v, int(ww)))
-        nbrs[v].append((u, int(ww)))
+        nbrs[int(u)].append((int(v), int(ww)))
+        nbrs[int(v)].append((int(u), int(ww)))
+    for l in nbrs:
+        l.sort()
+    return nbrs
+
+
+def initial_blocks(PS: np.ndarray, k: int, init: str = "kd") -> np.ndarray:
+    """Initial blocks of the partitioner: init "kd", the kd median split of the
+    sample points (`kd_labels`, ties: vertex index); init "hilbert", the
+    sample vertices in Hilbert order (ties: vertex index) cut into k
+    consecutive runs, block = floor(rank * k / eta)."""
+    eta, D = PS.shape
+    if init == "kd":
+        return kd_labels(PS, k)
+    bits = hilbert_bits(D)
+    q = quantize(PS, bits)
+    keys = np.array([hilbert_key(q[i], bits) for i in range(eta)], dtype=np.int64)
+    order = np.lexsort((np.arange(eta), keys))
+    block = np.empty(eta, dtype=np.int64)
+    block[order] = (np.arange(eta) * k) // eta
+    return block
+
+
+def lp_refine(nbrs, vw, block: np.ndarray, k: int, lmin: int, lmax: int, rounds: int) -> np.ndarray:
+    """Synchronous size-constrained label propagation (the refinement step of
+    the partitioner).  Block weights W_b = sum of the vertex weights vw.  In
+    round r only vertices with v % 2 == r % 2 move.  A vertex's target is
+    the neighbouring block with the largest total edge weight to it (ties:
+    smaller block), if that beats its own block.  Candidates are taken in
+    vertex order: candidate v into block t from block a is accepted if
+    (weight of the earlier candidates into t) + vw[v] <= lmax - W_t and
+    (weight of the earlier candidates leaving a) + vw[v] <= W_a - lmin, the
+    earlier candidates counted whether or not they were accepted.  With unit
+    weights: the j-th candidate into t is accepted if j < lmax - |V_t|."""
+    n = len(vw)
+    block = np.array(block, dtype=np.int64)
     for r in range(rounds):
-        size = np.bincount(block, minlength=k)
-        target = np.full(eta, -1, dtype=np.int64)
-        for v in range(eta):
+        W = np.zeros(k, dtype=np.int64)
+        for v in range(n):
+            W[block[v]] += vw[v]
+        target = np.full(n, -1, dtype=np.int64)
+        for v in range(n):
             if v % 2 != r % 2:
                 continue
             conn = {}
@@ -197,20 +206,146 @@ def partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float =
                     best, bw = b, conn[b]
             if best >= 0 and bw > own:
                 target[v] = best
-        cnt_in = np.zeros(k, dtype=np.int64)
-        cnt_out = np.zeros(k, dtype=np.int64)
+        w_in = np.zeros(k, dtype=np.int64)
+        w_out = np.zeros(k, dtype=np.int64)
         moves = []
-        for v in range(eta):
+        for v in range(n):
             t = target[v]
             if t < 0:
                 continue
             a = block[v]
-            if cnt_in[t] < lmax - size[t] and cnt_out[a] < size[a] - lmin:
+            if w_in[t] + vw[v] <= lmax - W[t] and w_out[a] + vw[v] <= W[a] - lmin:
                 moves.append((v, t))
-            cnt_in[t] += 1
-            cnt_out[a] += 1
+            w_in[t] += vw[v]
+            w_out[a] += vw[v]
         for v, t in moves:
             block[v] = t
+    return block
+
+
+def partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float = 0.05,
+              rounds: int = 16, init: str = "kd") -> np.ndarray:
+    """Size-constrained k-way partition of the sample graph by one level of
+    label propagation (stands in for KaHIP, which is not available):
+    `initial_blocks`, then `rounds` rounds of `lp_refine` with unit vertex
+    weights and the bounds of `partition_bounds`."""
+    eta, D = PS.shape
+    if k <= 1:
+        return np.zeros(eta, dtype=np.int64)
+    lmin, lmax = partition_bounds(eta, k, eps)
+    return lp_refine(adjacency(eta, E, w), [1] * eta, initial_blocks(PS, k, init), k, lmin, lmax, rounds)
+
+
+def match_heavy_edges(nbrs, vw, block: np.ndarray, cmax: int, sweeps: int = 4) -> np.ndarray:
+    """Coarsening step of the multilevel partitioner: a matching of heavy
+    edges inside the blocks, found by handshakes.  In each of `sweeps`
+    synchronous sweeps every unmatched vertex v prefers its unmatched
+    neighbour u with block[u] == block[v] and vw[u] + vw[v] <= cmax that has
+    the heaviest edge to it (ties: smaller u); v and u are matched when each
+    prefers the other.  Returns mate (-1: unmatched)."""
+    n = len(vw)
+    mate = np.full(n, -1, dtype=np.int64)
+    for _ in range(sweeps):
+        pref = np.full(n, -1, dtype=np.int64)
+        for v in range(n):
+            if mate[v] >= 0:
+                continue
+            best, bw = -1, -1
+            for u, ww in nbrs[v]:
+                if mate[u] >= 0 or block[u] != block[v] or vw[u] + vw[v] > cmax:
+                    continue
+                if ww > bw:
+                    best, bw = u, ww
+            pref[v] = best
+        for v in range(n):
+            if mate[v] < 0 and pref[v] >= 0 and pref[pref[v]] == v:
+                mate[v] = pref[v]
+    return mate
+
+
+def contract(nbrs, vw, block: np.ndarray, mate: np.ndarray):
+    """The coarse graph of a matching: every pair (and every unmatched vertex)
+    becomes one coarse vertex, numbered in the order of its smaller fine
+    vertex; its weight is the pair's total, its block the pair's block; the
+    weight of a coarse edge is the total weight of the fine edges between
+    its ends (edges inside a pair vanish).  Returns (coarse nbrs, coarse vw,
+    coarse block, cmap: fine vertex -> coarse vertex)."""
+    n = len(vw)
+    rep = np.array([min(v, mate[v]) if mate[v] >= 0 else v for v in range(n)], dtype=np.int64)
+    cid = np.full(n, -1, dtype=np.int64)
+    nc = 0
+    for v in range(n):
+        if rep[v] == v:
+            cid[v] = nc
+            nc += 1
+    cmap = cid[rep]
+    cvw = [0] * nc
+    cblock = np.zeros(nc, dtype=np.int64)
+    acc = [dict() for _ in range(nc)]
+    for v in range(n):
+        a = int(cmap[v])
+        cvw[a] += vw[v]
+        cblock[a] = block[v]
+        for u, ww in nbrs[v]:
+            b = int(cmap[u])
+            if b != a:
+                acc[a][b] = acc[a].get(b, 0) + ww
+    cnbrs = [sorted(d.items()) for d in acc]
+    return cnbrs, cvw, cblock, cmap
+
+
+def ml_partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float = 0.05,
+                 rounds: int = 16, init: str = "kd", sweeps: int = 4, max_levels: int = 12,
+                 trace: dict | None = None) -> np.ndarray:
+    """Multilevel size-constrained k-way partition of the sample graph (a
+    multilevel scheme in the manner of KaHIP, which is not available),
+    deterministic:
+
+    1. initial blocks (`initial_blocks`) on the sample graph itself;
+    2. coarsening: `match_heavy_edges` inside the blocks with coarse vertices
+       of weight at most cmax = max(2, floor(lmax / 4)), then `contract`;
+       repeated until a level keeps more than 95 % of its vertices (that
+       level is dropped) or `max_levels` levels exist.  The coarse graphs
+       inherit the blocks, so every level has the same block weights;
+    3. uncoarsening: from the coarsest level to the sample graph, `rounds`
+       rounds of `lp_refine` with the coarse vertex weights, then the
+       blocks are projected to the next finer level (a fine vertex takes its
+       coarse vertex's block).  Moving a coarse vertex moves a whole cluster
+       of sample vertices.
+    trace (optional): filled with the per-level vertex counts, matchings,
+    maps and blocks."""
+    eta, D = PS.shape
+    if k <= 1:
+        return np.zeros(eta, dtype=np.int64)
+    lmin, lmax = partition_bounds(eta, k, eps)
+    cmax = max(2, lmax // 4)
+    levels = [(adjacency(eta, E, w), [1] * eta)]
+    block = initial_blocks(PS, k, init)
+    blocks = [block]
+    cmaps = []
+    while len(levels) < max_levels:
+        nbrs, vw = levels[-1]
+        mate = match_heavy_edges(nbrs, vw, blocks[-1], cmax, sweeps)
+        cnbrs, cvw, cblock, cmap = contract(nbrs, vw, blocks[-1], mate)
+        if len(cvw) > 0.95 * len(vw):
+            break
+        if trace is not None:
+            trace.setdefault("mates", []).append(mate)
+        levels.append((cnbrs, cvw))
+        blocks.append(cblock)
+        cmaps.append(cmap)
+    block = blocks[-1]
+    for lev in range(len(levels) - 1, -1, -1):
+        nbrs, vw = levels[lev]
+        block = lp_refine(nbrs, vw, block, k, lmin, lmax, rounds)
+        if trace is not None:
+            trace.setdefault("refined", []).append(block.copy())
+        if lev > 0:
+            block = block[cmaps[lev - 1]]
+    if trace is not None:
+        trace["sizes"] = [len(vw) for _, vw in levels]
+        trace["cmaps"] = cmaps
+        trace["coarse"] = [(nb, vw) for nb, vw in levels[1:]]
     return block
 
 

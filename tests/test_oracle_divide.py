@@ -263,3 +263,109 @@ def test_bfs_border_misses_an_island(orc):
     assert B2 < B1
     assert np.array_equal(dv.merge(parts, B1, V1, P, lab), want)
     assert not np.array_equal(dv.merge(parts, B2, V2, P, lab), want)
+
+
+def _golden_partition():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "partition_lp_ml.txt")
+    g = {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        g[key] = vals
+    return g
+
+
+def _edges_of(vals):
+    t = np.array([int(x) for x in vals], dtype=np.int64).reshape(-1, 3)
+    return t[:, :2], t[:, 2]
+
+
+def test_lp_refine_hand_derived_rounds():
+    """Tie-break (smaller block), parity of the moving vertices, and the
+    acceptance order (earlier candidates counted whether accepted or not)
+    against a case worked out on paper (tests/golden/partition_lp_ml.txt)."""
+    g = _golden_partition()
+    n, k, eps = int(g["lp.n"][0]), int(g["lp.k"][0]), float(g["lp.eps"][0])
+    E, w = _edges_of(g["lp.edges"])
+    lmin, lmax = dv.partition_bounds(n, k, eps)
+    assert (lmin, lmax) == (2, 4)
+    nbrs = dv.adjacency(n, E, w)
+    init = np.array([int(x) for x in g["lp.init"]])
+    one = dv.lp_refine(nbrs, [1] * n, init, k, lmin, lmax, 1)
+    two = dv.lp_refine(nbrs, [1] * n, init, k, lmin, lmax, 2)
+    assert one.tolist() == [int(x) for x in g["lp.after1"]]
+    assert two.tolist() == [int(x) for x in g["lp.after2"]]
+
+
+def test_multilevel_hand_derived_case():
+    """Heavy-edge matching, contraction and the coarse move of a bound pair
+    that single-vertex moves cannot make (tests/golden/partition_lp_ml.txt)."""
+    g = _golden_partition()
+    n, k, eps = int(g["ml.n"][0]), int(g["ml.k"][0]), float(g["ml.eps"][0])
+    E, w = _edges_of(g["ml.edges"])
+    PS = np.stack([np.arange(n, dtype=np.float64), np.zeros(n)], axis=1)
+    assert dv.partition(PS, E, w, k, eps, rounds=2).tolist() == [int(x) for x in g["ml.lp2"]]
+    tr = {}
+    got = dv.ml_partition(PS, E, w, k, eps, rounds=2, trace=tr)
+    assert tr["sizes"] == [8, 4]
+    assert tr["mates"][0].tolist() == [int(x) for x in g["ml.mate"]]
+    assert tr["cmaps"][0].tolist() == [int(x) for x in g["ml.cmap"]]
+    cnbrs, cvw = tr["coarse"][0]
+    assert cvw == [2, 2, 2, 2]
+    ce = sorted((a, b, ww) for a in range(4) for b, ww in cnbrs[a] if a < b)
+    want = [int(x) for x in g["ml.coarse_edges"]]
+    assert ce == [tuple(want[i:i + 3]) for i in range(0, len(want), 3)]
+    assert tr["refined"][0].tolist() == [int(x) for x in g["ml.coarse_refined"]]
+    assert got.tolist() == [int(x) for x in g["ml.result"]]
+    assert dv.cut_weight(E, w, got) == 1 and dv.cut_weight(E, w, dv.partition(PS, E, w, k, eps, rounds=2)) == 20
+
+
+@pytest.mark.parametrize("k,init", [(4, "kd"), (16, "kd"), (16, "hilbert")])
+def test_multilevel_invariants(k, init):
+    """On a sample graph: every block weight within [lmin, lmax] at the end,
+    every coarse level a contraction of the one below (vertex weights sum to
+    eta, coarse vertices at most cmax), and a cut no heavier than the
+    initial blocks'."""
+    P = pointsets.clustered(60_000, 5)
+    ids = dv.sample_ids(len(P), 1200, 3)
+    PS = P[ids]
+    E, w = dv.sample_graph(PS, ids)
+    lmin, lmax = dv.partition_bounds(len(PS), k, 0.05)
+    tr = {}
+    b = dv.ml_partition(PS, E, w, k, 0.05, rounds=8, init=init, trace=tr)
+    sizes = np.bincount(b, minlength=k)
+    assert sizes.min() >= lmin and sizes.max() <= lmax
+    assert len(tr["sizes"]) >= 2 and all(a > b2 for a, b2 in zip(tr["sizes"], tr["sizes"][1:]))
+    for _, cvw in tr["coarse"]:
+        assert sum(cvw) == len(PS) and max(cvw) <= max(2, lmax // 4)
+    assert dv.cut_weight(E, w, b) <= dv.cut_weight(E, w, dv.initial_blocks(PS, k, init))
+
+
+def test_lp_refine_counts_rejected_candidates():
+    """A rejected candidate still counts against its target's room
+    (tests/golden/partition_lp_ml.txt, case LP2)."""
+    g = _golden_partition()
+    n, k, eps = int(g["lp2.n"][0]), int(g["lp2.k"][0]), float(g["lp2.eps"][0])
+    E, w = _edges_of(g["lp2.edges"])
+    lmin, lmax = dv.partition_bounds(n, k, eps)
+    assert (lmin, lmax) == (3, 5)
+    init = np.array([int(x) for x in g["lp2.init"]])
+    got = dv.lp_refine(dv.adjacency(n, E, w), [1] * n, init, k, lmin, lmax, 1)
+    assert got.tolist() == [int(x) for x in g["lp2.after1"]]
+
+
+def test_matching_hand_derived():
+    """Handshake matching: ties to the smaller neighbour, no pair across
+    blocks, the weight cap (tests/golden/partition_lp_ml.txt, case M)."""
+    g = _golden_partition()
+    n = int(g["m.n"][0])
+    E, w = _edges_of(g["m.edges"])
+    block = np.array([int(x) for x in g["m.block"]])
+    nbrs = dv.adjacency(n, E, w)
+    cmax = int(g["m.cmax"][0])
+    assert dv.match_heavy_edges(nbrs, [1] * n, block, cmax, 4).tolist() == [int(x) for x in g["m.mate_unit"]]
+    vw = [int(x) for x in g["m.weights"]]
+    assert dv.match_heavy_edges(nbrs, vw, block, cmax, 4).tolist() == [int(x) for x in g["m.mate_weighted"]]
