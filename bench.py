@@ -1,17 +1,24 @@
 #!/usr/bin/env python
-"""Throughput benchmark of the GB300 divide-and-conquer Delaunay triangulation.
+"""Throughput and latency benchmark of the GB300 divide-and-conquer Delaunay triangulation.
 
-Workload (default ``uniform3d_1m``): 3D, 1,000,000 points uniform in [0,1]^3
-(float64, seed 2), k = 16 partitions from a 0.5% sample (Alg. 1 + Alg. 2),
-grid border primitive, log edge weights.  One step = one full
-dt_triangulate: divide, 16 partial triangulations, border detection, border
-triangulation, hash merge and canonical output, all on the GPU.
+Workload (default ``clustered3d_4m``): 3D, 4,000,000 float64 points (seed 3):
+80 % from 50 Gaussian blobs, 20 % on a noisy heightfield; k = 64 partitions
+from a 0.5 % sample (Alg. 1 + Alg. 2), grid border primitive, log edge
+weights.  One step = one full dt_triangulate: divide, 64 partial
+triangulations, border detection, border triangulation, hash merge,
+neighbourhood update and canonical output, all on the GPU.
 
 Printed (rank 0, one JSON line): Mpoints/s over the K timed steps (inputs
-resident in HBM, L2 flushed before every step), the same metric end to end
-through the C ABI from pinned host buffers (host<->device copies inside the
-timed region), the roofline of the dominant kernel measured live with CUDA
-events, the CPU oracle timed on a bounded sample, and the SM clocks seen.
+resident in HBM, L2 flushed before every step); beside it, on the same GPU
+and points, the plain path (k = 1), the kd median divide (Sec. 2.3) with its
+partition metrics, the 1M uniform workload as a secondary line, and a short
+serving leg (Poisson arrivals of 3D jobs: p50/p99 latency of the served form
+and of the plain path replayed under the same arrivals); the same metric end
+to end through the C ABI from pinned host buffers (host<->device copies
+inside the timed region); the roofline of the dominant kernel from the
+algorithmic bytes and flops per triangulated point, with its CUDA-event time
+measured live; the FP32/FP64 FMA roofs measured live; the CPU oracle timed on
+a bounded sample; and the SM clocks seen.
 
 ``--impl reference`` times the CPU oracle instead (the only reference that
 exists for this method: the paper ships no code), on a bounded sample.
@@ -22,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -77,44 +85,64 @@ def gen_points(w, seed_offset=0):
     return pointsets.clustered(w["n"], w["seed"] + seed_offset)
 
 
-# FP32 FMA rate of one GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.070 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic work per triangulated point (3D, uniform; 2D in brackets):
+# bytes = 24 coordinates + ~56 label/scatter + ~108 simplices written (6.77 x
+# 16 B) + ~108 adjacency + ~25 border and hash = 320 B [90 B]; flops = ~20
+# insphere filters x ~70 + ~30 orient filters x ~25 + the border
+# circumspheres = ~2.3 kflop [0.6 kflop].  The points a step triangulates are
+# n + eta + |vertices(B)| (the partitions, the sample and the border set).
+ALG_BYTES_PER_POINT = {3: 320.0, 2: 90.0}
+ALG_FLOPS_PER_POINT = {3: 2300.0, 2: 600.0}
+# flops of one conflict test's first (FP32) stage, by dimension: determinant and both permanents
+TEST_FLOPS = {3: 220.0, 2: 70.0}
 
 
-def make_roofline(prof_tot: dict, prof_step_ms: list, n: int, steps: int, peaks: dict, peak_src: str):
+def make_roofline(prof_tot: dict, prof_step_ms: list, units: int, dim: int, steps: int, peaks: dict,
+                  peak_src: str, fma: dict | None = None, n: int | None = None):
     """Roofline of the kernel with the largest total time in the profiled
     steps (prof_tot: name -> {"ms", "launches", "bytes", "flops"} summed over
-    `steps` steps; prof_step_ms: each profiled step's time).  achieved =
-    algorithmic bytes per launch / mean launch time, against the HBM peak;
-    traffic = the stored ncu DRAM bytes per point scaled to one launch (when
-    taken on the current kernel source); `alu` = the same kernel's
-    conflict-test arithmetic against the derived FP32 rate."""
+    `steps` steps; prof_step_ms: each profiled step's time; units: points
+    triangulated per step).  achieved = ALG_BYTES_PER_POINT x units per step /
+    the kernel's time per step (= the per-launch bytes over the mean launch
+    time), against the measured HBM copy bandwidth.  The kernel's own count of
+    the bytes it gathers is reported beside it (gather_bytes_per_launch), not
+    as `achieved`.  fp64 / fp32: ALG_FLOPS_PER_POINT x units against the FMA
+    rates measured live (fma: {"fp32": TF/s, "fp64": TF/s}).  traffic = the
+    stored ncu DRAM bytes per input point (n points) scaled to one launch,
+    when taken on the current kernel source."""
     dom = max(prof_tot.items(), key=lambda kv: kv[1]["ms"]) if prof_tot else None
-    if not dom:
+    if not dom or units <= 0:
         return None
     name, a = dom
+    steps = max(steps, 1)
+    launches_per_step = a["launches"] / steps
+    kernel_s = a["ms"] / steps / 1e3                              # kernel time per step
+    alg_bytes = ALG_BYTES_PER_POINT[dim] * units                  # per step
+    achieved = alg_bytes / kernel_s / 1e9 if kernel_s > 0 else 0.0
     per_launch_ms = a["ms"] / max(a["launches"], 1)
-    bytes_per_launch = a["bytes"] / max(a["launches"], 1)
-    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
     bpp = stored_cavity_traffic() if name == "k_cavity_w<3>" else None
-    traffic = bpp * n / max(a["launches"] / max(steps, 1), 1) if bpp else None
+    traffic = bpp * (n or units) / max(launches_per_step, 1) if bpp else None
+    tests = a["flops"] / TEST_FLOPS[dim] / steps
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "traffic_source": ("ncu DRAM bytes on uniform3d_200k (host-driven rounds) scaled by points; "
-                                   "profiles/k_cavity_w_traffic.md") if traffic else None,
+                "algorithmic": f"{ALG_BYTES_PER_POINT[dim]:.0f} B per triangulated point x {units} points "
+                               f"(n + eta + |vertices(B)|) per step, over the kernel's CUDA-event time per step",
+                "bytes_per_launch": alg_bytes / max(launches_per_step, 1), "ms_per_launch": per_launch_ms,
+                "launches_per_step": launches_per_step,
+                "gather_bytes_per_launch": a["bytes"] / max(a["launches"], 1),
+                "traffic_source": ("ncu DRAM bytes per input point (uniform3d_200k, host-driven rounds) scaled to "
+                                   "one launch; profiles/k_cavity_w_traffic.md") if traffic else None,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
                 "share_of_step": a["ms"] / sum(prof_step_ms) if sum(prof_step_ms) > 0 else None,
-                "timing": "CUDA events around every launch, K profiled steps after the timed region",
-                "filter_gflops": a["flops"] / (a["ms"] / 1e3) / 1e9 if a["ms"] > 0 else 0.0,
-                "launches": a["launches"], "ms_per_launch": per_launch_ms,
-                "bytes_per_launch": bytes_per_launch}
-    # second roof of the same kernel: the conflict-test arithmetic (FP32 first stage)
-    # against the FP32 rate derived from the unit counts and the maximum SM clock
-    filt = roofline["filter_gflops"] / 1e3
-    roofline["alu"] = {"bound": "alu", "achieved": filt, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": filt / FP32_PEAK_TFLOPS,
-                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                       "work": "220 flops per 3D conflict test (70 in 2D), counted per test on the device"}
+                "timing": "CUDA events around every launch, profiled steps after the timed region",
+                "conflict_tests_per_point": tests / units}
+    flops = ALG_FLOPS_PER_POINT[dim] * units / kernel_s / 1e12 if kernel_s > 0 else 0.0
+    for prec in ("fp64", "fp32"):
+        pk = (fma or {}).get(prec)
+        if pk:
+            roofline[prec] = {"bound": "alu", "achieved": flops, "peak": pk, "unit": "TFLOP/s", "frac": flops / pk,
+                              "peak_source": f"measured live: dt_measure_fma_rate({prec[2:]}), FMA chains on every SM",
+                              "work": f"{ALG_FLOPS_PER_POINT[dim]:.0f} flops per triangulated point"}
     return roofline
 
 
@@ -122,7 +150,7 @@ def cavity_fingerprint() -> str:
     """SHA-1 of the source of the dominant kernel (region growth + k_cavity_w):
     a stored DRAM-traffic figure only applies to the kernel it was taken on."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_1902_07554_gb300", "csrc", "engine.cu")).read()
+    src = open(os.path.join(ROOT, "paper_1902_07554_gb300", "csrc", "engine_core.cuh")).read()
     a = src.find("__device__ __forceinline__ void grow_region(")
     b = src.find("// Second growth of large region")
     return hashlib.sha1(src[a:b].encode()).hexdigest() if a >= 0 and b > a else ""
@@ -458,7 +486,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform3d_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="clustered3d_4m", choices=sorted(WORKLOADS))
+    ap.add_argument("--frac", default=None,
+                    help="sample size: a fraction of n, 'sqrt' (eta = sqrt n) or 'logn' (eta = log2 n); default: the "
+                         "workload's")
+    ap.add_argument("--weight", default=None, choices=["log", "constant", "inverse", "linear"],
+                    help="edge weights of the sample graph (Table 1); default log")
+    ap.add_argument("--partitioner", default="lp", choices=["lp", "ml"],
+                    help="sample-graph partitioner: one level of label propagation, or multilevel")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 1M uniform secondary line")
+    ap.add_argument("--no-serve-leg", action="store_true", help="skip the short serving leg")
+    ap.add_argument("--serve-jobs", type=int, default=40, help="jobs of the short serving leg")
     ap.add_argument("--divide", default="sample", choices=["sample", "kd"])
     ap.add_argument("--autotune", action="store_true",
                     help="time the candidate insertion schedules on the workload first and use the fastest")
@@ -487,20 +525,39 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    from paper_1902_07554_gb300 import Triangulator
+    from paper_1902_07554_gb300 import Triangulator, fma_rate
     stream = torch.cuda.Stream(device=local)       # one explicit stream for torch and the library
     torch.cuda.set_stream(stream)
     # neighbors=1: the merge's neighbourhood update runs inside every step
     tri = Triangulator(local, stream=stream.cuda_stream, divide=0 if args.divide == "sample" else 1,
                        profile=1 if args.host_rounds else 0, neighbors=1, recursive=1 if args.recursive else 0)
+    sample_frac = parse_frac(args.frac, w["frac"], w["n"])
+    if args.weight:
+        tri.configure(weight=args.weight)
+    tri.configure(partitioner=1 if args.partitioner == "ml" else 0)
     P = gen_points(w, seed_offset=rank)
     n = w["n"]
     P_dev = torch.from_numpy(P).to(f"cuda:{local}")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")   # > L2 (129 MB)
     torch.cuda.synchronize()
 
+    def steps_ms(points, k, count):
+        """CUDA-event time of `count` dt_triangulate calls, L2 flushed before each."""
+        out, nl = [], 0
+        for _ in range(count):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tri.triangulate(points, k=k, sample_frac=sample_frac, fetch=False)
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+            nl += tri.stats().launches
+        return out, nl
+
     for _ in range(args.warmup):
-        tri.triangulate(P_dev, k=w["k"], sample_frac=w["frac"], fetch=False)
+        tri.triangulate(P_dev, k=w["k"], sample_frac=sample_frac, fetch=False)
 
     # ---------------- timed region: K steps on device-resident inputs (no per-kernel events)
     clk = ClockSampler(local)
@@ -509,18 +566,7 @@ def main():
     torch.cuda.synchronize()
     clk.start()
     t0 = time.perf_counter()
-    step_ms = []
-    launches = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tri.triangulate(P_dev, k=w["k"], sample_frac=w["frac"], fetch=False)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        launches += tri.stats().launches
+    step_ms, launches = steps_ms(P_dev, w["k"], args.steps)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = clk.stop()
@@ -530,38 +576,39 @@ def main():
     ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
     value = job_value(n, world, ms_max)
     stats = tri.stats().as_dict()
+    units = int(n + (stats["eta"] if stats["k"] > 1 else 0) + stats["border_vertices"])
 
     # ---------------- the plain path: the same points, same engine, k = 1 (no divide)
-    plain_ms = []
-    for _ in range(max(args.steps, 3)):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tri.triangulate(P_dev, k=1, sample_frac=w["frac"], fetch=False)
-        e1.record(stream)
-        e1.synchronize()
-        plain_ms.append(e0.elapsed_time(e1))
+    plain_ms, _ = steps_ms(P_dev, 1, max(args.steps // 2, 3))
     plain_step = max_over_ranks(sum(plain_ms) / len(plain_ms), dist, f"cuda:{local}")
     plain = {"value": job_value(n, world, plain_step), "unit": "Mpoints/s", "ms_per_step": plain_step,
              "what": "dt_triangulate with k = 1: the same insertion engine on all points, no divide, "
                      "no border triangulation, no merge"}
 
-    # ---------------- per-kernel times: the same K steps again with CUDA events
-    # around every engine launch (kept out of the timed region: the events
-    # themselves cost host time in the short rounds)
+    # ---------------- the other divide on the same points (sample <-> kd median, Sec. 2.3)
+    other = "kd" if args.divide == "sample" else "sample"
+    comparator = None
+    if not args.recursive and w["k"] > 1:
+        tri.configure(divide=1 if other == "kd" else 0)
+        tri.triangulate(P_dev, k=w["k"], sample_frac=sample_frac, fetch=False)
+        cmp_ms, _ = steps_ms(P_dev, w["k"], max(args.steps // 2, 3))
+        cst = tri.stats().as_dict()
+        tri.configure(divide=0 if args.divide == "sample" else 1)
+        cmp_step = max_over_ranks(sum(cmp_ms) / len(cmp_ms), dist, f"cuda:{local}")
+        comparator = {"divide": other, "value": job_value(n, world, cmp_step), "unit": "Mpoints/s",
+                      "ms_per_step": cmp_step,
+                      **{k: cst[k] for k in ("border_vertices", "border_simplices", "imbalance", "cv", "o_dt")}}
+
+    # ---------------- per-kernel times: profiled steps with CUDA events around
+    # every engine launch (kept out of the timed region: the events themselves
+    # cost host time in the short rounds)
     tri.configure(profile=1)
     prof_tot = {}
     prof_step_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tri.triangulate(P_dev, k=w["k"], sample_frac=w["frac"], fetch=False)
-        e1.record(stream)
-        e1.synchronize()
-        prof_step_ms.append(e0.elapsed_time(e1))
+    nprof = max(1, min(args.steps, 5))
+    for _ in range(nprof):
+        ms1, _ = steps_ms(P_dev, w["k"], 1)
+        prof_step_ms += ms1
         for kp in tri.kernel_profile():
             a = prof_tot.setdefault(kp["name"], dict(ms=0.0, launches=0, bytes=0.0, flops=0.0))
             for key in ("ms", "launches", "bytes", "flops"):
@@ -577,7 +624,7 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        tri.triangulate(P_pin, k=w["k"], sample_frac=w["frac"], fetch=False)
+        tri.triangulate(P_pin, k=w["k"], sample_frac=sample_frac, fetch=False)
         cnt = tri.simplex_count()
         tri.simplices(out=out_pin[:cnt])
         e2e_ms.append(1e3 * (time.perf_counter() - t))
@@ -586,6 +633,32 @@ def main():
            "h2d_bytes_per_step": int(n * w["dim"] * 8), "d2h_bytes_per_step": int(cnt * (w["dim"] + 1) * 4),
            "ms_per_step": e2e_step}
 
+    # ---------------- secondary workload (the 1M uniform configuration), fewer steps
+    secondary = None
+    if args.workload != "uniform3d_1m" and not args.no_secondary and w["dim"] == 3:
+        w2 = WORKLOADS["uniform3d_1m"]
+        P2 = torch.from_numpy(gen_points(w2, seed_offset=rank)).to(f"cuda:{local}")
+        tri.triangulate(P2, k=w2["k"], sample_frac=w2["frac"], fetch=False)
+        sec_ms, _ = steps_ms(P2, w2["k"], max(args.steps // 4, 3))
+        st2 = tri.stats().as_dict()
+        pl2_ms, _ = steps_ms(P2, 1, max(args.steps // 4, 3))
+        secondary = {"workload": "uniform3d_1m", "n": w2["n"], "k": w2["k"], "sample_frac": w2["frac"],
+                     "value": job_value(w2["n"], world, max_over_ranks(sum(sec_ms) / len(sec_ms), dist,
+                                                                        f"cuda:{local}")),
+                     "ms_per_step": sum(sec_ms) / len(sec_ms),
+                     "plain_path": job_value(w2["n"], world, max_over_ranks(sum(pl2_ms) / len(pl2_ms), dist,
+                                                                            f"cuda:{local}")),
+                     **{k: st2[k] for k in ("border_vertices", "imbalance", "cv", "o_dt")}}
+        del P2
+
+    # ---------------- latency under load: a short serving leg on this GPU
+    latency = None
+    if not args.no_serve_leg and rank == 0 and w["dim"] == 3:
+        tri.close()
+        torch.cuda.synchronize()
+        latency = serving_leg(local, jobs=args.serve_jobs, load=0.8, seed=5)
+        tri = None
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -593,8 +666,10 @@ def main():
 
     # ---------------- roofline of the dominant kernel (live CUDA-event times)
     peaks, peak_src = load_peaks()
-    roofline = make_roofline(prof_tot, prof_step_ms, n, args.steps, peaks, peak_src)
-    kernels = {k: {"ms": round(v["ms"], 3), "launches": v["launches"]} for k, v in prof_tot.items()}
+    fma = {"fp32": fma_rate(local, 32, 5), "fp64": fma_rate(local, 64, 5)}
+    roofline = make_roofline(prof_tot, prof_step_ms, units, w["dim"], nprof, peaks, peak_src, fma, n=n)
+    kernels = {k: {"ms_per_step": round(v["ms"] / nprof, 3), "launches_per_step": v["launches"] / nprof}
+               for k, v in prof_tot.items()}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -604,22 +679,81 @@ def main():
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "dim": w["dim"], "k": w["k"], "sample_frac": w["frac"],
+        "config": {"workload": args.workload, "n": n, "dim": w["dim"], "k": w["k"], "sample_frac": sample_frac,
                    "divide": args.divide + (" recursive bisection" if args.recursive else ""),
-                   "primitive": "grid", "weight": "log", "neighbors": True,
+                   "primitive": "grid", "weight": args.weight or "log", "neighbors": True,
+                   "partitioner": "multilevel" if args.partitioner == "ml" else "label propagation",
                    "rounds": "host-driven (profile mode)" if args.host_rounds else "one CUDA graph per engine run",
                    "l2": "flushed before every step (256 MiB write); working set > L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "e2e": e2e, "plain_path": plain, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-        "gpu_launches": int(launches),
+        "e2e": e2e, "plain_path": plain, "divide_comparator": comparator, "latency": latency,
+        "secondary": secondary, "roofline": roofline, "fma_peaks_tflops": fma, "cpu_baseline": cpu,
+        "clocks": clocks, "gpu_launches": int(launches),
         "stats": {k: stats[k] for k in ("simplices", "eta", "border_vertices", "border_simplices", "imbalance",
                                          "cv", "o_dt", "rounds_max", "exact_calls", "ms_phase")},
+        "triangulated_points_per_step": units,
         "kernels": kernels, "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def parse_frac(arg, default, n: int):
+    """Sample size of Sec. 4.2 as the library's sample_frac: a fraction of n,
+    'sqrt' (eta = ceil(sqrt n), the paper's default; the library reads 0 so)
+    or 'logn' (eta = ceil(log2 n), passed as a fraction that rounds up to it)."""
+    if arg is None:
+        return default
+    if arg == "sqrt":
+        return 0.0
+    if arg == "logn":
+        return (math.ceil(math.log2(n)) - 0.5) / n
+    return float(arg)
+
+
+def serving_leg(device: int, jobs: int = 40, load: float = 0.8, seed: int = 5) -> dict:
+    """Latency under load on this GPU: `jobs` 3D jobs (sizes log-uniform in
+    1,000..2,000,000, half uniform, half clustered) arriving as a Poisson
+    stream at `load` x the plain path's measured capacity.  Served form: the
+    continuous-batching server.  Plain path: one context, k = 1, no batching,
+    jobs taken first in, first out under the SAME arrival times (replayed on
+    the clock, not simulated).  Latency = arrival to simplices on the host."""
+    from paper_1902_07554_gb300 import Triangulator
+    from paper_1902_07554_gb300.serve import Job, Server, poisson_arrivals
+    sizes, kinds, seeds = pointsets.serve_jobs(jobs, seed=seed)
+    pts = [pointsets.job_points(sizes[i], kinds[i], seeds[i]) for i in range(jobs)]
+    total = int(sum(len(p) for p in pts))
+    plain = Triangulator(device)
+    plain.triangulate(pts[0][:5000], k=1, fetch=False)
+    service = []
+    for P in pts:                                   # capacity of the plain path (jobs back to back)
+        t = time.perf_counter()
+        plain.triangulate(P, k=1, fetch=True)
+        service.append(time.perf_counter() - t)
+    cap = total / sum(service)
+    rate = load * cap / (total / jobs)
+    arr = poisson_arrivals(jobs, rate, seed)
+    # plain path replayed under the same arrivals
+    lat = []
+    t0 = time.perf_counter()
+    for a, P in zip(arr, pts):
+        delay = a - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        plain.triangulate(P, k=1, fetch=True)
+        lat.append(time.perf_counter() - t0 - a)
+    span = time.perf_counter() - t0 - arr[0]
+    plain.close()
+    lat = np.array(lat)
+    plain_sum = {"throughput_mpts": total / span / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "capacity_mpts": cap / 1e6}
+    srv = Server(device=device, keep_results=False)
+    served = srv.run([Job(float(arr[i]), i, pts[i]) for i in range(jobs)])
+    keep = ("throughput_mpts", "p50_ms", "p99_ms", "mean_ms", "makespan_s", "peak_reserved_gb", "batched_jobs")
+    return {"jobs": jobs, "points": total, "offered_load": load, "budget_gb": 120,
+            "served": {k: served[k] for k in keep if k in served}, "plain": plain_sum}
 
 
 if __name__ == "__main__":

@@ -76,6 +76,14 @@ extern "C" {
 #define DT_INIT_HILBERT 1    /* k equal ranges of the sample in Hilbert-curve order */
 #define DT_INIT_KD 2         /* the kd median split of the sample (the cuts of DT_DIVIDE_KD) */
 
+/* Partitioners of the sample graph (stand-ins for KaHIP, Sec. 4.3). */
+#define DT_PART_LP 0         /* the initial blocks refined by lp_rounds rounds of size-constrained label
+                                propagation on the sample graph */
+#define DT_PART_MULTILEVEL 1 /* multilevel: heavy-edge matchings inside the initial blocks coarsen the
+                                graph level by level, then lp_rounds rounds of label propagation with
+                                vertex weights refine every level from the coarsest down (a coarse move
+                                moves a whole cluster of sample points) */
+
 /* Edge weights of the sample graph (Table 1). */
 #define DT_WEIGHT_LOG 0
 #define DT_WEIGHT_CONSTANT 1
@@ -110,6 +118,20 @@ typedef struct dt_config {
   int recursive;         /* 1: recursive bisection (Sec. 3.1): the divide applied log2 k times with
                             k' = 2 (a fresh sample per node, or the kd median split) and k - 1 merges,
                             batched level by level; k must be a power of two */
+  int active_ratio;      /* continuous activation: before every insertion round further BRIO levels are
+                            activated while the active set holds fewer than active_ratio / 100 x the
+                            points inserted so far (and at least first_batch per instance); 0 = the
+                            drain rule of brio_drain */
+  int nominate_rings;    /* a nominee must hold the strongest pick of this round within this many
+                            neighbour rings of its located simplex (1 or 2); 0 = automatic (1) */
+  int partitioner;       /* DT_PART_*: the partitioner of the sample graph; default DT_PART_LP */
+  int round_limit;       /* insertion rounds of one engine run before it stops with DT_E_TIMEOUT;
+                            0 = 400,000 */
+  int walk_limit;        /* steps of one point-location walk before DT_E_TIMEOUT; 0 = 65,536 */
+  int arena_factor;      /* simplex slots per point of the insertion arena (dead slots are not reused,
+                            so a 3D run needs about 27); an arena that overflows is doubled and the run
+                            repeated, three times at most, then the call fails with DT_E_OVERFLOW;
+                            0 = automatic (36 in 3D, 8 in 2D) */
 } dt_config;
 
 typedef struct dt_stats {

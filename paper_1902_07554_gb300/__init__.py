@@ -51,7 +51,9 @@ class Config(ctypes.Structure):
                 ("cavity_cap", ctypes.c_int), ("profile", ctypes.c_int), ("neighbors", ctypes.c_int),
                 ("first_batch", ctypes.c_int), ("brio_growth", ctypes.c_int),
                 ("small_rounds", ctypes.c_int), ("brio_drain", ctypes.c_int),
-                ("partition_init", ctypes.c_int), ("recursive", ctypes.c_int)]
+                ("partition_init", ctypes.c_int), ("recursive", ctypes.c_int),
+                ("active_ratio", ctypes.c_int), ("nominate_rings", ctypes.c_int), ("partitioner", ctypes.c_int),
+                ("round_limit", ctypes.c_int), ("walk_limit", ctypes.c_int), ("arena_factor", ctypes.c_int)]
 
 
 class KernelProfile(ctypes.Structure):
@@ -131,6 +133,7 @@ def load_library(build: bool = True):
         "dt_get_batch_simplices": ([p, p, i64, p, p], i32),
         "dt_get_batch_status": ([p, p, i32], i32),
         "dt_select_sample_noalloc": ([i32, p, i64, i64, ctypes.c_uint64, p], i32),
+        "dt_measure_fma_rate": ([i32, i32, i32, p], i32),
         "dt_get_neighbors": ([p, p, i64, p], i32),
         "dt_validate": ([p, p, i64, i32, p, i64, p], i32),
         "dt_submit": ([p, p, i64, i32, i32, dbl, p], i32),
@@ -144,6 +147,16 @@ def load_library(build: bool = True):
         fn.restype = res
     _lib = L
     return L
+
+
+def fma_rate(device: int = 0, precision: int = 64, reps: int = 5) -> float:
+    """Measured FP32 or FP64 FMA throughput of the device (TFLOP/s)."""
+    L = load_library()
+    out = ctypes.c_double(0.0)
+    rc = L.dt_measure_fma_rate(device, precision, reps, ctypes.byref(out))
+    if rc:
+        raise DTError(rc, "dt_measure_fma_rate failed")
+    return out.value
 
 
 def _ptr(a):

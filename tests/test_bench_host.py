@@ -38,25 +38,42 @@ def test_stored_traffic_only_for_the_kernel_it_was_taken_on(monkeypatch):
     assert bench.stored_cavity_traffic() is None
 
 
-def test_derived_fp32_roof():
-    assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.07e-3)
-
-
 def test_roofline_from_profiled_kernel_times():
-    """The dominant kernel's roofline from per-kernel totals over K profiled
-    steps (the figures of a measured 1M-point run)."""
+    """The dominant kernel's roofline from per-kernel totals over 5 profiled
+    steps: 320 B and 2.3 kflop per triangulated point (1,265,715 points per
+    step: n + eta + |vertices(B)| of a measured 1M-point run) over the
+    kernel's time per step (319.261 ms / 5 = 63.8522 ms)."""
     launches = 3787
     prof = {"k_cavity_w<3>": {"ms": 319.261, "launches": launches, "bytes": 36927271.45814629 * launches,
-                              "flops": 487.258486271189e9 * 0.319261},
+                              "flops": 220.0 * 141e6 * 5},
             "k_insert_w<3>": {"ms": 103.117, "launches": launches, "bytes": 0.0, "flops": 0.0}}
-    r = bench.make_roofline(prof, [150.0] * 5, 1_000_000, 5, {"hbm_gbs": 6800.7}, "measured")
+    fma = {"fp64": 1.2, "fp32": 70.0}
+    r = bench.make_roofline(prof, [150.0] * 5, 1_265_715, 3, 5, {"hbm_gbs": 6800.7}, "measured", fma,
+                            n=1_000_000)
     assert r["kernel"] == "k_cavity_w<3>" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["achieved"] == pytest.approx(438.02, rel=1e-4)
-    assert r["frac"] == pytest.approx(438.02 / 6800.7, rel=1e-4)
+    # 320 x 1,265,715 = 405,028,800 B per step over 63.8522 ms
+    assert r["achieved"] == pytest.approx(6.34322, rel=1e-4)
+    assert r["frac"] == pytest.approx(6.34322 / 6800.7, rel=1e-4)
+    assert r["bytes_per_launch"] == pytest.approx(405_028_800 / (3787 / 5), rel=1e-9)
+    assert r["gather_bytes_per_launch"] == pytest.approx(36927271.45814629)
     assert r["share_of_step"] == pytest.approx(319.261 / 750.0)
-    assert r["alu"]["achieved"] == pytest.approx(0.48726, rel=1e-4)
-    assert r["alu"]["frac"] == pytest.approx(0.48726 / bench.FP32_PEAK_TFLOPS, rel=1e-4)
+    # 2,300 x 1,265,715 = 2.9111445e9 flops per step over 63.8522 ms
+    assert r["fp64"]["achieved"] == pytest.approx(0.0455919, rel=1e-4)
+    assert r["fp64"]["frac"] == pytest.approx(0.0455919 / 1.2, rel=1e-4)
+    assert r["fp32"]["frac"] == pytest.approx(0.0455919 / 70.0, rel=1e-4)
+    assert r["conflict_tests_per_point"] == pytest.approx(141e6 / 1_265_715)
     stored = bench.stored_cavity_traffic()
-    if stored is not None:   # DRAM bytes per point scaled to one launch (launches per step = 3787 / 5)
+    if stored is not None:   # DRAM bytes per input point scaled to one launch (launches per step = 3787 / 5)
         assert r["traffic"] == pytest.approx(stored * 1_000_000 / (launches / 5))
-    assert bench.make_roofline({}, [], 1, 1, {"hbm_gbs": 1.0}, "fallback") is None
+    assert bench.make_roofline({}, [], 1, 3, 1, {"hbm_gbs": 1.0}, "fallback") is None
+
+
+def test_sample_size_flags():
+    """--frac: a fraction, 'sqrt' (the library's 0) or 'logn' (rounds up to ceil(log2 n))."""
+    import math
+    assert bench.parse_frac(None, 0.005, 10) == 0.005
+    assert bench.parse_frac("0.02", 0.005, 10) == 0.02
+    assert bench.parse_frac("sqrt", 0.005, 10) == 0.0
+    for n in (1_000_000, 4_000_000, 10_000):
+        f = bench.parse_frac("logn", 0.005, n)
+        assert math.ceil(f * n) == math.ceil(math.log2(n))
