@@ -5,12 +5,12 @@ benchmark times.
   compared element by element with the oracle's DT (integer output:
   bit-exact), for the sample divide, the kd median divide and recursive
   bisection.
-* 4,000,000 clustered 3D points, k = 64: the full oracle DT takes minutes on
-  the host, so the output is certified on the device (local Delaunay, hull
-  convexity, Euler characteristic, every point a vertex), must equal the
-  direct k = 1 result and the kd-divide result, and a random sample of its
-  simplices is checked one by one with the oracle's exact predicates against
-  every point near its circumsphere.
+* 4,000,000 clustered 3D points, k = 64, 0.5 % sample: the whole output is
+  compared element by element with the oracle's DT (a few minutes of one
+  host core), for the sample divide and the kd divide; the device
+  certificate (local Delaunay, hull convexity, Euler characteristic, every
+  point a vertex) and an exact empty-sphere check of sampled simplices run
+  beside it as independent checks.
 """
 import numpy as np
 import pytest
@@ -77,7 +77,7 @@ def _empty_sphere_sample(P, S, m, seed):
     return len(tuples)
 
 
-def test_clustered3d_4m_k64_certified(tri):
+def test_clustered3d_4m_k64_matches_oracle(tri):
     P = pointsets.workload("clustered3d_4m")
     tri.configure(validate=1, neighbors=1)
     try:
@@ -85,13 +85,13 @@ def test_clustered3d_4m_k64_certified(tri):
         st = tri.stats()
     finally:
         tri.configure(validate=0, neighbors=0)
-    assert st.k == 64 and st.validated == 1
-    assert _empty_sphere_sample(P, S, 300, 5) > 0
-    direct = tri.triangulate(P, k=1, sample_frac=0.0).astype(np.int64)
-    assert np.array_equal(direct, S)
+    assert st.k == 64 and st.validated == 1 and st.border_vertices > 0
     tri.configure(divide=1)
     try:
         kd = tri.triangulate(P, k=64, sample_frac=0.005).astype(np.int64)
     finally:
         tri.configure(divide=0)
-    assert np.array_equal(kd, S)
+    want = oracle.delaunay(P)
+    assert np.array_equal(S, want)
+    assert np.array_equal(kd, want)
+    assert _empty_sphere_sample(P, S, 300, 5) > 0

@@ -50,3 +50,21 @@ def test_admission_respects_the_budget():
                  batch_points=60_000, keep_results=False)
     srv.run(jobs)
     assert srv.peak_reserved <= budget
+
+
+def test_large_job_in_the_mix_matches_oracle():
+    """A 1.5M-point clustered 3D job served among smaller ones that arrive
+    while it runs equals the oracle's DT of that job, element by element."""
+    from paper_1902_07554_gb300.serve import Job, Server
+    big = pointsets.job_points(1_500_000, "clustered", 12345)
+    jobs = [Job(0.0, 0, big)]
+    sizes, kinds, seeds = pointsets.serve_jobs(10, seed=21, lo=1000, hi=100_000)
+    for i in range(10):
+        jobs.append(Job(0.01 * (i + 1), i + 1, pointsets.job_points(sizes[i], kinds[i], seeds[i])))
+    srv = Server(workers=3)
+    summary = srv.run(jobs)
+    assert summary["jobs"] == 11
+    res = {r.jid: r for r in srv.results()}
+    assert np.array_equal(res[0].simplices.astype(np.int64), oracle.delaunay(big))
+    for j in jobs[1:]:
+        assert np.array_equal(res[j.jid].simplices.astype(np.int64), oracle.delaunay(j.points)), j.jid
