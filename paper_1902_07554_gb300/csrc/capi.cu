@@ -41,7 +41,10 @@ static bool cfg_valid(const dt_config* c) {
          c->cavity_cap <= 4096 && c->first_batch >= 0 &&
          (c->brio_growth == 0 || (c->brio_growth > 100 && c->brio_growth <= 10000)) && c->small_rounds >= -1 &&
          c->brio_drain >= 0 && c->brio_drain <= 64 && c->partition_init >= 0 && c->partition_init <= 2 &&
-         (c->recursive == 0 || c->recursive == 1);
+         (c->recursive == 0 || c->recursive == 1) && c->active_ratio >= 0 && c->active_ratio <= 10000 &&
+         c->nominate_rings >= 0 && c->nominate_rings <= 2 && (c->partitioner == DT_PART_LP ||
+         c->partitioner == DT_PART_MULTILEVEL) && c->round_limit >= 0 && c->walk_limit >= 0 &&
+         c->arena_factor >= 0 && c->arena_factor <= 1024;
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {
@@ -99,6 +102,11 @@ extern "C" void dt_destroy(dt_ctx* c) {
   for (int i = 0; i < 16; i++) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   for (int i = 0; i < 16; i++) if (c->pev[i]) cudaEventDestroy(c->pev[i]);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  for (auto& rg : c->round_graphs) {
+    if (rg.gx) cudaGraphExecDestroy(rg.gx);
+    if (rg.g) cudaGraphDestroy(rg.g);
+  }
+  c->round_graphs.clear();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();

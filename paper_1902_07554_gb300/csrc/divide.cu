@@ -430,6 +430,7 @@ int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, d
     if (rc) return rc;
     k_initial_blocks<<<g, 256, (++c->launches, 0), s>>>(idx, eta, k, block);
   }
+  if (c->cfg.partitioner == DT_PART_MULTILEVEL) return partition_multilevel(c, G, k, eps, rounds, block);
   int lmin, lmax;
   partition_bounds(eta, k, eps, &lmin, &lmax);
   for (int r = 0; r < rounds; r++) {

@@ -27,6 +27,7 @@ int graph_bbox(dt_ctx* c, int dim, const void* PS, int64_t eta, double* box);
 void partition_bounds(int64_t eta, int k, double eps, int* lmin, int* lmax);
 int partition_graph(dt_ctx* c, const void* PS, int dim, SampleGraph& G, int k, double eps, int rounds, int init,
                     int* block);
+int partition_multilevel(dt_ctx* c, const SampleGraph& G, int k, double eps, int rounds, int* block);
 int cut_weight(dt_ctx* c, const SampleGraph& G, const int* block, long long* out);
 int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, const int* srank, const SampleGraph& G,
                  const int* block, int* label, int* nearest);

@@ -26,7 +26,7 @@ def tri():
 
 def _cfg(tri, **kw):
     base = dict(divide=0, primitive=0, weight=0, lp_rounds=16, epsilon=0.05, grid_cell=1.0, seed=1,
-                base_threshold=16, validate=0, cavity_cap=0, recursive=0, partition_init=0)
+                base_threshold=16, validate=0, cavity_cap=0, recursive=0, partition_init=0, partitioner=0)
     base.update(kw)
     tri.configure(**base)
 
@@ -157,6 +157,30 @@ def test_partition_graph_entry(tri):
             assert np.array_equal(got.astype(np.int64), dv.partition(P[ids], E, w, k, init="hilbert"))
     finally:
         tri.configure(partition_init="auto")
+
+
+@pytest.mark.parametrize("gen,D,eta,k,init", [("normal", 2, 500, 3, "kd"), ("normal", 2, 500, 16, "kd"),
+                                               ("clustered", 3, 3000, 64, "kd"), ("uniform", 3, 2000, 16, "hilbert"),
+                                               ("clustered", 3, 20000, 64, "kd")])
+def test_multilevel_partition_matches_oracle(tri, gen, D, eta, k, init):
+    """The multilevel partitioner (matchings inside the blocks, contraction,
+    weighted label propagation on every level) gives the oracle's blocks bit
+    for bit, down to the full 0.5 % sample of the 4M clustered workload."""
+    n = eta * 100 if gen != "normal" else 5000
+    P = {"normal": lambda: pointsets.normal(n, D, 12), "uniform": lambda: pointsets.uniform(n, D, 5),
+         "clustered": lambda: pointsets.clustered(n, 7)}[gen]()
+    ids = dv.sample_ids(len(P), eta, 3)
+    E, w = dv.sample_graph(P[ids], ids)
+    _cfg(tri, partitioner=1, partition_init=init)
+    try:
+        got = tri.partition_graph(P[ids], E, w, k, 0.05, 16).astype(np.int64)
+    finally:
+        _cfg(tri, partitioner=0, partition_init="auto")
+    want = dv.ml_partition(P[ids], E, w, k, 0.05, 16, init=init)
+    assert np.array_equal(got, want)
+    lmin, lmax = dv.partition_bounds(eta, k, 0.05)
+    sizes = np.bincount(got, minlength=k)
+    assert sizes.min() >= lmin and sizes.max() <= lmax
 
 
 @pytest.mark.parametrize("D,n,k,frac,divide", [(2, 20000, 4, 0.01, 0), (2, 20000, 8, 0.01, 1),
