@@ -14,6 +14,12 @@ struct dt_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;     // capture stream of the insertion-round graph
   bool pdl_ok = true;                    // programmatic launches accepted in the round graph
+  // instantiated round graphs, keyed by the bytes of every launch parameter
+  // captured in them: a run whose buffers, sizes and grids equal an earlier
+  // run's relaunches that run's graph instead of capturing a new one
+  struct RoundGraph { std::string key; cudaGraph_t g = nullptr; cudaGraphExec_t gx = nullptr; };
+  std::vector<RoundGraph> round_graphs;
+  long long graphs_built = 0, graphs_reused = 0;
   bool own_stream = false;
   dt_config cfg;
   std::string err;

@@ -58,6 +58,8 @@ struct TriView {
   const int* toff;          // per instance: first simplex slot
   int ninst;
   unsigned long long* dbg;  // walk statistics (debug runs only; null otherwise)
+  int rings;                // neighbour rings a nominee must hold the strongest pick in (1 or 2)
+  int walk_limit;           // steps of one location walk before DT_E_TIMEOUT
 };
 
 struct CandScratch {

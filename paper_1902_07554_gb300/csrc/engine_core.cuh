@@ -1,4 +1,8 @@
-// engine.cu -- batched parallel Bowyer-Watson insertion (see engine.cuh).
+// engine_core.cuh -- batched parallel Bowyer-Watson insertion (see engine.cuh).
+//
+// Included by engine.cu (the 2D instantiation and the functions shared by both
+// dimensions, GDT_ENGINE_SHARED) and by engine3.cu (the 3D instantiation), so
+// that the two dimensions compile as separate translation units in parallel.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -19,21 +23,21 @@ constexpr int TAGBIT = (int)0x80000000;
 // Round key of point p: (round, hash of p and round, pass bit).  The pass bit
 // is set when a large region is grown a second time (k_cavity_big): the
 // nominee then outranks its own first-pass claims but no other nominee.
-__device__ __forceinline__ unsigned long long mkkey(unsigned round, int p) {
+static __device__ __forceinline__ unsigned long long mkkey(unsigned round, int p) {
   return ((unsigned long long)round << 33) |
          ((unsigned long long)fmix32((uint32_t)p ^ (round * 0x9E3779B9u)) << 1);
 }
-__device__ __forceinline__ int get4(const int4& v, int i) {
+static __device__ __forceinline__ int get4(const int4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
-__device__ __forceinline__ void set4(int4& v, int i, int x) {
+static __device__ __forceinline__ void set4(int4& v, int i, int x) {
   if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
 }
-__device__ __forceinline__ int* comp_ptr(int4* a, int s, int i) { return reinterpret_cast<int*>(a + s) + i; }
+static __device__ __forceinline__ int* comp_ptr(int4* a, int s, int i) { return reinterpret_cast<int*>(a + s) + i; }
 
 // Appends `val` to list/counter for the lanes with pred set; every lane of
 // the warp must call this.
-__device__ __forceinline__ void warp_append(int* list, int* counter, bool pred, int val) {
+static __device__ __forceinline__ void warp_append(int* list, int* counter, bool pred, int val) {
   unsigned mask = __ballot_sync(0xffffffffu, pred);
   if (!mask) return;
   int lane = threadIdx.x & 31;
@@ -44,7 +48,7 @@ __device__ __forceinline__ void warp_append(int* list, int* counter, bool pred, 
   if (pred) list[base + __popc(mask & ((1u << lane) - 1))] = val;
 }
 
-__device__ __forceinline__ bool collinear3(double4_32a a, double4_32a b, double4_32a c) {
+static __device__ __forceinline__ bool collinear3(double4_32a a, double4_32a b, double4_32a c) {
   double2 pa, pb, pc;
   pa = make_double2(a.x, a.y); pb = make_double2(b.x, b.y); pc = make_double2(c.x, c.y);
   if (orient2(pa, pb, pc) != 0) return false;
@@ -130,6 +134,10 @@ struct EngCtl {
   int drain;           // the next batch is activated when the active set is last_batch / drain
   int small;           // 1: the next rounds are small enough for k_small_rounds (one CTA)
   int small_max;       // active points up to which a round counts as small
+  float ratio;         // > 0: continuous activation (active set kept near ratio x points inserted)
+  int min_active;      // continuous activation: the active set's floor
+  long long activated_total;   // points activated so far (continuous activation)
+  int round_limit;     // rounds before the run stops with DT_E_TIMEOUT
 };
 
 // Programmatic dependent launch inside the round graph: each round kernel
@@ -137,7 +145,7 @@ struct EngCtl {
 // memory is then visible), then lets the next one start launching, so that
 // the next launch overlaps this kernel's run.  Both are no-ops in a launch
 // without the programmatic attribute.
-__device__ __forceinline__ void pdl_enter() {
+static __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;");
 }
@@ -273,14 +281,14 @@ enum { CAND_OK = 0, CAND_LOST = 1, CAND_OVER = 2 };
 // first: the cavity kernel takes them in that order, so the regions of strong
 // nominees are claimed early and weaker ones stop at their first contact.
 constexpr int NBUCKET = 8;
-__device__ __forceinline__ int key_bucket(unsigned long long key) {
+static __device__ __forceinline__ int key_bucket(unsigned long long key) {
   return NBUCKET - 1 - (int)((key >> 30) & 7);   // the top 3 bits of the hash
 }
 
 // Slot -> nominee: slots enumerate the buckets in order (bcnt: bucket sizes,
 // of which the first seg entries are stored; seg: the capacity of one list).
 // The caller keeps slot below the number stored, which k_nominate counts.
-__device__ __forceinline__ int nominee_at(const int* nom, const int* bcnt, int seg, int slot) {
+static __device__ __forceinline__ int nominee_at(const int* nom, const int* bcnt, int seg, int slot) {
   int q = 0, base = 0;
 #pragma unroll
   for (int b = 0; b < NBUCKET - 1; b++) {
@@ -289,6 +297,23 @@ __device__ __forceinline__ int nominee_at(const int* nom, const int* bcnt, int s
     else break;
   }
   return nom[(int64_t)q * seg + (slot - base)];
+}
+
+// Is a key stronger than `key` picked in a simplex of the second ring of t0
+// (the neighbours of t0's neighbours)?
+template <int D>
+__device__ __forceinline__ bool stronger_in_ring2(const TriView<D>& T, int t0, const int4& nn0,
+                                                  unsigned long long key) {
+  for (int i = 0; i <= D; i++) {
+    const int u = nb_simplex(get4(nn0, i));
+    if (!slot_ok(T, u)) continue;
+    const int4 nu = T.tn[u];
+    for (int j = 0; j <= D; j++) {
+      const int w = nb_simplex(get4(nu, j));
+      if (w != t0 && slot_ok(T, w) && *((volatile unsigned long long*)&T.claimC[w]) > key) return true;
+    }
+  }
+  return false;
 }
 
 template <int D>
@@ -319,6 +344,8 @@ __global__ void __launch_bounds__(256) k_nominate(TriView<D> T, const int* act, 
         int u = nb_simplex(get4(nn0, i));
         if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) take = false;
       }
+      // a stronger pick two rings away would most likely claim part of this region too
+      if (take && T.rings > 1 && stronger_in_ring2(T, t0, nn0, key)) take = false;
     }
     if (take) bucket = key_bucket(key);
   }
@@ -824,10 +851,10 @@ __device__ __forceinline__ void activate_warp(const TriView<D>& T, const int* li
       if (!(slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p])) h = T.hint2[g];
       if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
     }
-    for (int hop = 0; hop < (1 << 16) && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
+    for (int hop = 0; hop < T.walk_limit && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
       s = nb_simplex(*comp_ptr(T.tn, s, 0));
     int steps = 0;
-    int r = walk_to(T, s, p, 1 << 16, &steps);
+    int r = walk_to(T, s, p, T.walk_limit, &steps);
     if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
     if (r < 0) {
       set_error(T.st, DT_E_TIMEOUT, 4);
@@ -894,7 +921,7 @@ template <int D>
 __device__ __forceinline__ void reloc_walk_one(const TriView<D>& T, int p, unsigned next_round) {
   int s = nb_simplex(*comp_ptr(T.tn, T.loc[p], 0));
   int steps = 0;
-  int r = walk_to(T, s, p, 1 << 16, &steps);
+  int r = walk_to(T, s, p, T.walk_limit, &steps);
   if (r < 0) { set_error(T.st, DT_E_TIMEOUT, 3); return; }
   T.loc[p] = r;
   atomicMax(&T.claimC[r], mkkey(next_round, p));
@@ -917,7 +944,7 @@ __global__ void __launch_bounds__(128, 8) k_reloc_walk(TriView<D> T, const int* 
     reloc_walk_one<D>(T, walk[idx], next_round);
 }
 
-__device__ __forceinline__ unsigned long long ord_key(double x) {
+static __device__ __forceinline__ unsigned long long ord_key(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x + 0.0);
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
@@ -933,12 +960,12 @@ __global__ void k_make_x32(const typename PT<D>::T* pts, const int* pinst, int64
                       (float)o[3]);
 }
 
-__global__ void k_scatter_levels(const int* level, const int* rank, const int* loff, int64_t n, int* list) {
+static __global__ void k_scatter_levels(const int* level, const int* rank, const int* loff, int64_t n, int* list) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p < n && level[p] >= 0) list[loff[level[p]] + rank[p]] = (int)p;
 }
 
-__global__ void k_move_count(int* dst, int* src) {
+static __global__ void k_move_count(int* dst, int* src) {
   *dst = *src;
   *src = 0;
 }
@@ -946,16 +973,25 @@ __global__ void k_move_count(int* dst, int* src) {
 // Start of a device-driven round: activate the next level(s) when the active
 // set has drained to a quarter of the last batch (the rule of the host
 // loop), advance the round, clear the round's counters.
-__device__ void round_begin(EngCtl& C, int* cnt, const int* loffd) {
+static __device__ void round_begin(EngCtl& C, int* cnt, const int* loffd) {
   int nact = cnt[0];
   int lo = -1, hi = -1;
-  while (C.next_level >= 0 && nact <= C.last_batch / C.drain) {
+  // drain rule: the next level(s) once the active set has drained to
+  // last_batch / drain; continuous rule: levels while the active set is
+  // below ratio x the points inserted so far (activated - still active)
+  auto wants = [&]() {
+    if (C.ratio <= 0.0f) return nact <= C.last_batch / C.drain;
+    const long long inserted = C.activated_total - nact;
+    return (long long)nact < max((long long)C.min_active, (long long)(C.ratio * (float)inserted));
+  };
+  while (C.next_level >= 0 && wants()) {
     const int l = C.next_level;
     const int m = loffd[l + 1] - loffd[l];
     if (m > 0) {
       if (hi < 0) hi = loffd[l + 1];
       lo = loffd[l];
       nact += m;
+      C.activated_total += m;
       C.last_batch = nact;
     }
     C.next_level--;
@@ -965,13 +1001,13 @@ __device__ void round_begin(EngCtl& C, int* cnt, const int* loffd) {
   C.activated = C.act_n;
   C.small = nact <= C.small_max ? 1 : 0;
   if (nact > 0) C.round++;
-  if (C.round > 400000 && C.done == 0) C.done = 4;
+  if (C.round > (unsigned)C.round_limit && C.done == 0) C.done = 4;
   cnt[1] = cnt[2] = cnt[3] = cnt[4] = cnt[5] = 0;
   for (int b = 0; b < NBUCKET; b++) cnt[8 + b] = 0;
 }
 
 // The first round's start (before the loop).  One thread.
-__global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
+static __global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   round_begin(*ctl, cnt, loffd);
 }
@@ -980,7 +1016,7 @@ __global__ void k_round_begin(EngCtl* ctl, int* cnt, const int* loffd) {
 // becomes current; the loop ends when nothing is left, on a device error,
 // after 4 rounds in a row without an insertion (a cavity overflowed its
 // scratch: the host grows it), or at the round limit.  One thread.
-__device__ void round_end_begin(EngCtl& C, int* cnt, const int* loffd, const DevStatus* st) {
+static __device__ void round_end_begin(EngCtl& C, int* cnt, const int* loffd, const DevStatus* st) {
   const int had = cnt[0];
   const int nnew = cnt[1];
   cnt[0] = nnew;
@@ -998,7 +1034,7 @@ __device__ void round_end_begin(EngCtl& C, int* cnt, const int* loffd, const Dev
   if (C.done == 0) round_begin(C, cnt, loffd);
 }
 
-__global__ void k_round_step(EngCtl* ctl, int* cnt, const int* loffd, const DevStatus* st,
+static __global__ void k_round_step(EngCtl* ctl, int* cnt, const int* loffd, const DevStatus* st,
                              cudaGraphConditionalHandle handle) {
   pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1026,6 +1062,7 @@ __device__ __forceinline__ void nominate_warp(const TriView<D>& T, const int* ac
         const int u = nb_simplex(get4(nn0, i));
         if (slot_ok(T, u) && *((volatile unsigned long long*)&T.claimC[u]) > key) take = false;
       }
+      if (take && T.rings > 1 && stronger_in_ring2(T, t0, nn0, key)) take = false;
     }
   }
   warp_append(nom, nnom, take, p);
@@ -1131,6 +1168,7 @@ static cudaEvent_t prof_event(dt_ctx* c, size_t i) {
   return c->evpool[i];
 }
 
+#ifdef GDT_ENGINE_SHARED
 void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops) {
   for (auto& k : c->kprof)
     if (!strcmp(k.name, name)) {
@@ -1142,7 +1180,11 @@ void prof_add(dt_ctx* c, const char* name, double ms, double bytes, double flops
   c->kprof.push_back({name, ms > 0 ? 1 : 0, ms, bytes, flops});
 }
 
-int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool reset) {
+#endif
+
+// Exact-stage counters of this translation unit's predicates (each unit
+// holds its own copy of the device counters).
+static int pred_counters_local(dt_ctx* c, unsigned long long* calls, int* range, bool reset) {
   void* buf = pool_get(c, "predctr_eng", 64);
   if (!buf) return set_err(c, DT_E_NOMEM, "predicate counters");
   k_read_pred_counters<<<1, 1, (++c->launches, 0), c->stream>>>((unsigned long long*)buf, (int*)((char*)buf + 8), reset);
@@ -1154,6 +1196,7 @@ int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool 
   return 0;
 }
 
+#ifdef GDT_ENGINE_SHARED
 // FP32 copies of the points for the first predicate stage (see
 // predicates.cuh): per instance (pinst, or one instance when null) the
 // bounding box gives the origin o (its centre) and eta = 2 (u32 + 2 u64) R
@@ -1200,6 +1243,8 @@ int fp32_points(dt_ctx* c, int dim, const void* pts, const int* pinst, int64_t n
   return 0;
 }
 
+#endif
+
 // Scratch of the large regions (shared by every round; counter cnt[5]).
 static int big_scratch(dt_ctx* c, CandScratch& S, int* cnt) {
   S.capCbig = BIG_C;
@@ -1231,8 +1276,8 @@ static cudaStream_t capture_stream(dt_ctx* c) {
 template <int D>
 static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, int* cnt, const int* loffd,
                         const std::vector<int64_t>& loff, const int* llist, int* nom, int* walk, int* act0, int* act1,
-                        int nact, int last_batch, int next_level, int capC, int capB, unsigned* round_out,
-                        bool* failed) {
+                        int nact, int last_batch, int next_level, int capC, int capB, int min_active,
+                        unsigned* round_out, bool* failed) {
   cudaStream_t s = c->stream;
   cudaStream_t cs = capture_stream(c);
   EngCtl* ctl = (EngCtl*)pool_get(c, "eng.ctl", sizeof(EngCtl));
@@ -1246,6 +1291,10 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
   h0.last_nact = nact;
   h0.small_max = c->cfg.small_rounds > 0 ? c->cfg.small_rounds : -1;
   h0.drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
+  h0.ratio = c->cfg.active_ratio > 0 ? (float)c->cfg.active_ratio / 100.0f : 0.0f;
+  h0.min_active = min_active;
+  h0.activated_total = nact;
+  h0.round_limit = c->cfg.round_limit > 0 ? c->cfg.round_limit : 400000;
   CUDA_OK(cudaMemcpyAsync(ctl, &h0, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
   const int capCand = (int)std::max<int64_t>(1, std::min<int64_t>(npts, int64_t(1) << 22));
   int64_t max_level = 1;
@@ -1258,6 +1307,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
   memset(&h1, 0, sizeof(h1));
   for (int grow = 0;; grow++) {
     CandScratch S;
+    memset(&S, 0, sizeof(S));
     S.cap = capCand;
     S.capC = capC << grow;
     S.capB = capB << grow;
@@ -1269,9 +1319,30 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     S.count = cnt + 2;
     if (!S.cand || !S.meta || !S.cav || !S.bnd || !S.outer) return set_err(c, DT_E_NOMEM, "candidate scratch");
     { int rcb = big_scratch(c, S, cnt); if (rcb) return rcb; }
+    // every parameter baked into the graph: an equal key means an equal graph
+    std::string key;
+    auto put = [&](const void* p, size_t nb) { key.append((const char*)p, nb); };
+    const int dimk = D, pdlk = c->pdl_ok ? 1 : 0;
+    const void* ptrs[8] = {ctl, cnt, loffd, llist, nom, walk, c->status, cs};
+    const unsigned grids[4] = {gn, gr, ga, gw};
+    put(&dimk, 4); put(&pdlk, 4); put(&T, sizeof(T)); put(&S, sizeof(S)); put(ptrs, sizeof(ptrs));
+    put(grids, sizeof(grids)); put(&capCand, 4);
     cudaGraph_t g = nullptr;
     cudaGraphExec_t gx = nullptr;
-    cudaError_t e = cudaGraphCreate(&g, 0);
+    size_t cached = c->round_graphs.size();
+    for (size_t q = 0; q < c->round_graphs.size(); q++)
+      if (c->round_graphs[q].key == key) cached = q;
+    cudaError_t e = cudaSuccess;
+    if (cached < c->round_graphs.size()) {
+      gx = c->round_graphs[cached].gx;
+      c->graphs_reused++;
+      k_round_begin<<<1, 32, 0, s>>>(ctl, cnt, loffd);
+      e = cudaGraphLaunch(gx, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return set_err(c, gdt_cuda_fail(e, "round graph", __FILE__, __LINE__), "round graph");
+      gx = nullptr;
+    } else {
+    e = cudaGraphCreate(&g, 0);
     cudaGraphConditionalHandle hc = 0;
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
     cudaGraphNodeParams cp = {};
@@ -1329,9 +1400,22 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     if (e == cudaSuccess) k_round_begin<<<1, 32, 0, s>>>(ctl, cnt, loffd);
     if (e == cudaSuccess) e = cudaGraphLaunch(gx, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      // keep it for later runs with the same parameters (at most 16, oldest out)
+      if (c->round_graphs.size() >= 16) {
+        cudaGraphExecDestroy(c->round_graphs.front().gx);
+        cudaGraphDestroy(c->round_graphs.front().g);
+        c->round_graphs.erase(c->round_graphs.begin());
+      }
+      c->round_graphs.push_back({key, g, gx});
+      c->graphs_built++;
+      g = nullptr;
+      gx = nullptr;
+    }
     if (gx) cudaGraphExecDestroy(gx);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) return set_err(c, gdt_cuda_fail(e, "round graph", __FILE__, __LINE__), "round graph");
+    }
     const unsigned r0 = h1.round;
     CUDA_OK(cudaMemcpyAsync(&h1, ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -1371,7 +1455,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
   run.h_poff = poff;
   run.rounds = 0;
   // arena: per instance mult * n_i + pad slots
-  const int64_t mult = D == 2 ? 8 : 36, pad = 32;
+  const int64_t mult = c->cfg.arena_factor > 0 ? c->cfg.arena_factor : (D == 2 ? 8 : 36), pad = 32;
   int64_t grow = 1;
   for (int attempt = 0; attempt < 4; attempt++) {
     run.h_toff.assign(ninst + 1, 0);
@@ -1381,7 +1465,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     if (total >= (int64_t(1) << 29)) return set_err(c, DT_E_NOMEM, "simplex arena exceeds 2^29 slots");
     run.total_slots = total;
     unsigned long long calls0; int range0;
-    { int rc0 = pred_counters_engine(c, &calls0, &range0, false); if (rc0) return rc0; }
+    { int rc0 = pred_counters_local(c, &calls0, &range0, false); if (rc0) return rc0; }
     run.tv = pool_get(c, tag + ".tv", sizeof(int4) * total);
     run.tn = pool_get(c, tag + ".tn", sizeof(int4) * total);
     auto* claimA = (unsigned long long*)pool_get(c, tag + ".cA", 8 * total);
@@ -1413,6 +1497,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
 
     TriView<D> T;
+    memset(&T, 0, sizeof(T));   // padding too: the round-graph cache compares the bytes
     T.pts = (const P*)pts;
     T.gid = gid;
     T.pinst = pinst;
@@ -1429,6 +1514,8 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     T.npts = (int)npts;
     T.prof = nullptr;
     T.dbg = nullptr;
+    T.rings = c->cfg.nominate_rings > 1 ? 2 : 1;
+    T.walk_limit = c->cfg.walk_limit > 0 ? c->cfg.walk_limit : (1 << 16);
     if (getenv("GDT_DEBUG")) {
       T.dbg = (unsigned long long*)pool_get(c, "eng.dbg", 64);
       if (!T.dbg) return set_err(c, DT_E_NOMEM, "debug counters");
@@ -1534,6 +1621,9 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
                                                             act0, cnt);
     }
     int next_level = first_level - 1;    // next batch to activate (levels below are later)
+    // continuous activation keeps at least about first_batch points per instance active
+    const int min_active = (c->cfg.first_batch > 0 ? c->cfg.first_batch : 32) * std::max(ninst, 1);
+    const int round_limit = c->cfg.round_limit > 0 ? c->cfg.round_limit : 400000;
     int* h = c->counters_host;
     CUDA_OK(cudaMemcpyAsync(h, cnt, 4, cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
@@ -1558,7 +1648,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     const bool prof = c->cfg.profile != 0;
     const int SYNC_EVERY = 4;
     // profile records: (start event, end event, kernel)
-    struct ProfRec { int a, b, k; };
+    struct ProfRec { int a, b, k; unsigned r; };
     std::vector<ProfRec> recs;
     size_t nev = 0;
     auto mark = [&]() -> int {
@@ -1579,22 +1669,31 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       k_pick<D><<<(unsigned)ceil_div(nact, 256), 256, (++c->launches, 0), s>>>(T, ain, nact, 1);
     if (!host_loop && (nact > 0 || next_level >= 0)) {
       int rc = graph_rounds<D>(c, T, run, npts, cnt, loffd, loff, llist, nom, walk, act0, act1, nact, last_batch,
-                               next_level, capC, capB, &round, &failed);
+                               next_level, capC, capB, min_active, &round, &failed);
       if (rc) return rc;
       nact = 0;
       next_level = -1;
     }
+    // the activation rules of the device loop (round_begin); with continuous
+    // activation the host reads the active count after every round
+    const float ratio = c->cfg.active_ratio > 0 ? (float)c->cfg.active_ratio / 100.0f : 0.0f;
+    long long activated = nact;
+    auto wants = [&]() {
+      if (ratio <= 0.0f) return nact <= last_batch / drain;
+      const long long inserted = activated - nact;
+      return (long long)nact < std::max<long long>(min_active, (long long)(ratio * (float)inserted));
+    };
     while (nact > 0 || next_level >= 0) {
-      // activate the next batch when the active set has drained to a quarter
-      while (next_level >= 0 && nact <= last_batch / drain) {
+      while (next_level >= 0 && wants()) {
         int m = (int)(loff[next_level + 1] - loff[next_level]);
         if (m > 0) {
           const int a0 = mark();
           k_activate<D><<<(unsigned)ceil_div(m, 128), 128, (++c->launches, 0), s>>>(
               T, llist + loff[next_level], m, ain, cnt + 0, round + 1, nullptr);
           const int a1 = mark();
-          if (a0 >= 0 && a1 >= 0) recs.push_back({a0, a1, 5});
+          if (a0 >= 0 && a1 >= 0) recs.push_back({a0, a1, 5, round + 1});
           nact += m;
+          activated += m;
           last_batch = nact;
           last_sync_nact = -1;         // activation changes the count: skip one progress check
         }
@@ -1602,7 +1701,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       }
       if (nact <= 0) break;
       round++;
-      if (round > 400000) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
+      if (round > (unsigned)round_limit) return set_err(c, DT_E_TIMEOUT, "insertion rounds exceeded");
       int capCand = (int)std::min<int64_t>(nact, int64_t(1) << 22);
       CandScratch S;
       S.cap = capCand;
@@ -1637,7 +1736,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
                                                                                       nullptr);
       ev[5] = mark();
       for (int q = 0; q < 5; q++)
-        if (ev[q] >= 0 && ev[q + 1] >= 0) recs.push_back({ev[q], ev[q + 1], q});
+        if (ev[q] >= 0 && ev[q + 1] >= 0) recs.push_back({ev[q], ev[q + 1], q, round});
       if (getenv("GDT_DEBUG")) {
         int hc[5];
         unsigned long long hd[7];
@@ -1656,7 +1755,7 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       if (check)
         k_check_mesh<D><<<(unsigned)ceil_div<int64_t>(total, 256), 256, (++c->launches, 0), s>>>(
             T, run.toff, run.tcount, ninst, round);
-      if (round % SYNC_EVERY != 0 && nact > 4096 && !check) continue;
+      if (round % SYNC_EVERY != 0 && nact > 4096 && !check && ratio <= 0.0f) continue;
       CUDA_OK(cudaMemcpyAsync(h, cnt + 0, 4, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
@@ -1684,10 +1783,12 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     if (failed) { grow *= 2; continue; }
     if (prof && !recs.empty()) {
       CUDA_OK(cudaStreamSynchronize(s));
+      const bool roundlog = getenv("GDT_ROUNDLOG") != nullptr;   // per-round kernel times on stderr
       for (const ProfRec& r : recs) {
         float ms = 0;
         cudaEventElapsedTime(&ms, c->evpool[r.a], c->evpool[r.b]);
         prof_add(c, knames[D - 2][r.k], ms, 0, 0);
+        if (roundlog) fprintf(stderr, "rt %s %u %d %.4f\n", tag.c_str(), r.r, r.k, ms);
       }
     }
     if (profc) {
@@ -1708,18 +1809,12 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     CUDA_OK(cudaMemcpyAsync(run.h_tcount.data(), run.tcount, 4 * ninst, cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
     unsigned long long calls; int range;
-    int rc = pred_counters_engine(c, &calls, &range, false);
+    int rc = pred_counters_local(c, &calls, &range, false);
     if (rc) return rc;
     if (range != range0) return set_err(c, DT_E_RANGE, "coordinate range too wide for the exact fallback");
     return 0;
   }
   return set_err(c, DT_E_OVERFLOW, "simplex arena overflow after retries");
-}
-
-int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,
-               int64_t npts, const std::vector<int64_t>& poff, const std::string& tag) {
-  if (dim == 2) return engine_run_t<2>(c, run, pts, gid, pinst, npts, poff, tag);
-  return engine_run_t<3>(c, run, pts, gid, pinst, npts, poff, tag);
 }
 
 }  // namespace gdt
