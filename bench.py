@@ -55,7 +55,7 @@ WORKLOADS = {
     # 4,096 independent 2D instances, 256..65,536 points each (log-uniform)
     "batch2d_4096": dict(n=0, dim=2, gen="batch", seed=4, k=1, frac=0.0),
     # Poisson arrivals of 3D jobs, 1,000..2,000,000 points, uniform or clustered
-    "serve3d": dict(n=0, dim=3, gen="serve", seed=5, k=0, frac=0.005, jobs=120, load=0.8),
+    "serve3d": dict(n=0, dim=3, gen="serve", seed=5, k=0, frac=0.005),
 }
 
 
@@ -429,53 +429,31 @@ def ctypes_ptr(t):
 
 
 def run_serving(args, w):
-    """Continuous batching vs the plain path (one job at a time, k = 1, no
-    batching) on the same Poisson job stream at `load` x plain capacity."""
+    """The serving workload (Poisson arrivals of 3D jobs of 1,000..2,000,000
+    points, half uniform, half clustered, 120 GB budget): the served form and
+    the plain path under the same arrivals at offered loads 0.5, 0.8, 0.95
+    of the plain path's capacity and one overload point (1.2)."""
     import torch
-    from paper_1902_07554_gb300 import Triangulator
-    from paper_1902_07554_gb300.serve import Job, Server, k_for, poisson_arrivals
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    sizes, kinds, seeds = pointsets.serve_jobs(w["jobs"], seed=w["seed"])
-    pts = [pointsets.job_points(sizes[i], kinds[i], seeds[i]) for i in range(w["jobs"])]
+    pts = serving_jobs(args.serve_jobs, seed=w["seed"])
     total = int(sum(len(p) for p in pts))
-    # plain path: capacity and service times
-    plain = Triangulator(local)
-    plain.triangulate(pts[0][:5000], k=1, fetch=False)
-    service = []
-    for P in pts:
-        t = time.perf_counter()
-        plain.triangulate(P, k=1, fetch=True)
-        service.append(time.perf_counter() - t)
-    plain.close()
-    cap = total / sum(service)                                  # points per second
-    rate = w["load"] * cap / (total / len(pts))                 # jobs per second
-    arr = poisson_arrivals(len(pts), rate, w["seed"])
-    # plain path under the same arrivals: one server, FIFO
-    free, lat = 0.0, []
-    for a, sv in zip(arr, service):
-        start = max(a, free)
-        free = start + sv
-        lat.append(free - a)
-    lat = np.array(lat)
-    plain_sum = {"throughput_mpts": total / (free - arr[0]) / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "capacity_mpts": cap / 1e6}
-    jobs = [Job(float(arr[i]), i, pts[i], k=k_for(len(pts[i])), frac=w["frac"]) for i in range(len(pts))]
-    srv = Server(device=local, workers=3, budget_bytes=120e9, bytes_per_point=6000.0, keep_results=False)
+    service = plain_service_times(local, pts)
     clk = ClockSampler(local)
     clk.start()
-    served = srv.run(jobs)
+    legs = {str(load): serving_leg(local, pts, service, load, seed=w["seed"]) for load in (0.5, 0.8, 0.95, 1.2)}
     clocks = clk.stop()
+    main_leg = legs["0.8"]
     cpu = None if args.no_cpu_baseline else cpu_baseline_jobs(pts)
-    line = {"metric": METRIC, "value": served["throughput_mpts"], "unit": "Mpoints/s", "n_gpus": 1,
-            "steps": 1, "warmup": 1, "ms_per_step": served["makespan_s"] * 1e3, "higher_is_better": True,
+    line = {"metric": METRIC, "value": main_leg["served"]["throughput_mpts"], "unit": "Mpoints/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": main_leg["served"]["makespan_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "jobs": len(pts), "points": total, "offered_load": w["load"],
-                       "budget_gb": 120, "workers": 3},
-            "serve": {"served": served, "plain": plain_sum}, "clocks": clocks, "gpu_launches": served["launches"],
+            "config": {"workload": args.workload, "jobs": len(pts), "points": total, "offered_load": 0.8,
+                       "budget_gb": 120, "loads": [0.5, 0.8, 0.95, 1.2]},
+            "serve": legs, "clocks": clocks, "gpu_launches": main_leg["served"].get("launches"),
             "cpu_baseline": cpu,
-            "e2e": {"value": served["throughput_mpts"], "unit": "Mpoints/s",
-                    "h2d_bytes_per_step": total * 24, "d2h_bytes_per_step": int(served["rows_out"]) * 16}}
+            "e2e": {"value": main_leg["served"]["throughput_mpts"], "unit": "Mpoints/s",
+                    "h2d_bytes_per_step": total * 24, "d2h_bytes_per_step": None}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -496,7 +474,8 @@ def main():
                     help="sample-graph partitioner: one level of label propagation, or multilevel")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 1M uniform secondary line")
     ap.add_argument("--no-serve-leg", action="store_true", help="skip the short serving leg")
-    ap.add_argument("--serve-jobs", type=int, default=40, help="jobs of the short serving leg")
+    ap.add_argument("--serve-jobs", type=int, default=None,
+                    help="jobs of the serving leg (default 40) or of the serving workload (default 400)")
     ap.add_argument("--divide", default="sample", choices=["sample", "kd"])
     ap.add_argument("--autotune", action="store_true",
                     help="time the candidate insertion schedules on the workload first and use the fastest")
@@ -508,6 +487,8 @@ def main():
                          "kernel profiler lists each launch; the timed value then includes the event overhead")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.serve_jobs is None:
+        args.serve_jobs = 400 if w["gen"] == "serve" else 40
     if args.impl == "reference":
         return run_reference(args, w)
     if w["gen"] == "batch":
@@ -599,6 +580,21 @@ def main():
                       "ms_per_step": cmp_step,
                       **{k: cst[k] for k in ("border_vertices", "border_simplices", "imbalance", "cv", "o_dt")}}
 
+    # ---------------- the other partitioner of the sample graph (label propagation <-> multilevel)
+    part_cmp = None
+    if not args.recursive and w["k"] > 1 and args.divide == "sample":
+        other_ml = args.partitioner != "ml"
+        tri.configure(partitioner=1 if other_ml else 0)
+        tri.triangulate(P_dev, k=w["k"], sample_frac=sample_frac, fetch=False)
+        pm_ms, _ = steps_ms(P_dev, w["k"], max(args.steps // 2, 3))
+        pst = tri.stats().as_dict()
+        tri.configure(partitioner=0 if other_ml else 1)
+        pm_step = max_over_ranks(sum(pm_ms) / len(pm_ms), dist, f"cuda:{local}")
+        part_cmp = {"partitioner": "multilevel" if other_ml else "label propagation",
+                    "value": job_value(n, world, pm_step), "unit": "Mpoints/s", "ms_per_step": pm_step,
+                    "ms_partition_labels_scatter": pst["ms_phase"][1],
+                    **{k: pst[k] for k in ("border_vertices", "cut_weight", "imbalance", "cv", "o_dt")}}
+
     # ---------------- per-kernel times: profiled steps with CUDA events around
     # every engine launch (kept out of the timed region: the events themselves
     # cost host time in the short rounds)
@@ -656,7 +652,8 @@ def main():
     if not args.no_serve_leg and rank == 0 and w["dim"] == 3:
         tri.close()
         torch.cuda.synchronize()
-        latency = serving_leg(local, jobs=args.serve_jobs, load=0.8, seed=5)
+        spts = serving_jobs(args.serve_jobs, seed=5)
+        latency = serving_leg(local, spts, plain_service_times(local, spts), load=0.8, seed=5)
         tri = None
 
     if rank != 0:
@@ -686,11 +683,12 @@ def main():
                    "rounds": "host-driven (profile mode)" if args.host_rounds else "one CUDA graph per engine run",
                    "l2": "flushed before every step (256 MiB write); working set > L2",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "e2e": e2e, "plain_path": plain, "divide_comparator": comparator, "latency": latency,
+        "e2e": e2e, "plain_path": plain, "divide_comparator": comparator, "partitioner_comparator": part_cmp,
+        "latency": latency,
         "secondary": secondary, "roofline": roofline, "fma_peaks_tflops": fma, "cpu_baseline": cpu,
         "clocks": clocks, "gpu_launches": int(launches),
         "stats": {k: stats[k] for k in ("simplices", "eta", "border_vertices", "border_simplices", "imbalance",
-                                         "cv", "o_dt", "rounds_max", "exact_calls", "ms_phase")},
+                                         "cv", "o_dt", "cut_weight", "rounds_max", "exact_calls", "ms_phase")},
         "triangulated_points_per_step": units,
         "kernels": kernels, "wall_s": wall,
     }
@@ -713,46 +711,61 @@ def parse_frac(arg, default, n: int):
     return float(arg)
 
 
-def serving_leg(device: int, jobs: int = 40, load: float = 0.8, seed: int = 5) -> dict:
-    """Latency under load on this GPU: `jobs` 3D jobs (sizes log-uniform in
-    1,000..2,000,000, half uniform, half clustered) arriving as a Poisson
-    stream at `load` x the plain path's measured capacity.  Served form: the
-    continuous-batching server.  Plain path: one context, k = 1, no batching,
-    jobs taken first in, first out under the SAME arrival times (replayed on
-    the clock, not simulated).  Latency = arrival to simplices on the host."""
+def serving_jobs(jobs: int, seed: int = 5):
+    """The serving workload: `jobs` 3D jobs, sizes log-uniform in
+    1,000..2,000,000 points, half uniform, half clustered."""
+    sizes, kinds, seeds = pointsets.serve_jobs(jobs, seed=seed)
+    return [pointsets.job_points(sizes[i], kinds[i], seeds[i]) for i in range(jobs)]
+
+
+def plain_service_times(device: int, pts) -> list:
+    """The plain path (one context, k = 1, no batching) on every job back to
+    back, simplices copied to the host: seconds per job."""
+    from paper_1902_07554_gb300 import Triangulator
+    with Triangulator(device) as plain:
+        plain.triangulate(pts[0][:5000], k=1, fetch=False)
+        service = []
+        for P in pts:
+            t = time.perf_counter()
+            plain.triangulate(P, k=1, fetch=True)
+            service.append(time.perf_counter() - t)
+    return service
+
+
+def serving_leg(device: int, pts, service, load: float, seed: int = 5, budget: float = 120e9) -> dict:
+    """Latency under load on this GPU: the jobs arrive as a Poisson stream at
+    `load` x the plain path's measured capacity.  Served form: the
+    continuous-batching server (one resident engine, jobs admitted at round
+    boundaries, device memory from `budget`).  Plain path: one context, k = 1,
+    no batching, jobs taken first in, first out under the SAME arrival times
+    (replayed on the clock, not simulated).  Latency = arrival to simplices
+    on the host."""
     from paper_1902_07554_gb300 import Triangulator
     from paper_1902_07554_gb300.serve import Job, Server, poisson_arrivals
-    sizes, kinds, seeds = pointsets.serve_jobs(jobs, seed=seed)
-    pts = [pointsets.job_points(sizes[i], kinds[i], seeds[i]) for i in range(jobs)]
+    jobs = len(pts)
     total = int(sum(len(p) for p in pts))
-    plain = Triangulator(device)
-    plain.triangulate(pts[0][:5000], k=1, fetch=False)
-    service = []
-    for P in pts:                                   # capacity of the plain path (jobs back to back)
-        t = time.perf_counter()
-        plain.triangulate(P, k=1, fetch=True)
-        service.append(time.perf_counter() - t)
     cap = total / sum(service)
     rate = load * cap / (total / jobs)
     arr = poisson_arrivals(jobs, rate, seed)
-    # plain path replayed under the same arrivals
     lat = []
-    t0 = time.perf_counter()
-    for a, P in zip(arr, pts):
-        delay = a - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        plain.triangulate(P, k=1, fetch=True)
-        lat.append(time.perf_counter() - t0 - a)
-    span = time.perf_counter() - t0 - arr[0]
-    plain.close()
+    with Triangulator(device) as plain:
+        plain.triangulate(pts[0][:5000], k=1, fetch=False)
+        t0 = time.perf_counter()
+        for a, P in zip(arr, pts):
+            delay = a - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            plain.triangulate(P, k=1, fetch=True)
+            lat.append(time.perf_counter() - t0 - a)
+        span = time.perf_counter() - t0 - arr[0]
     lat = np.array(lat)
     plain_sum = {"throughput_mpts": total / span / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                  "p99_ms": float(np.percentile(lat, 99) * 1e3), "capacity_mpts": cap / 1e6}
-    srv = Server(device=device, keep_results=False)
+    srv = Server(device=device, dim=3, budget_bytes=budget, keep_results=False)
     served = srv.run([Job(float(arr[i]), i, pts[i]) for i in range(jobs)])
-    keep = ("throughput_mpts", "p50_ms", "p99_ms", "mean_ms", "makespan_s", "peak_reserved_gb", "batched_jobs")
-    return {"jobs": jobs, "points": total, "offered_load": load, "budget_gb": 120,
+    keep = ("throughput_mpts", "p50_ms", "p99_ms", "mean_ms", "makespan_s", "failed", "capacity_points",
+            "peak_running_points", "device_gb", "quanta", "rounds", "launches", "model_bytes_per_point")
+    return {"jobs": jobs, "points": total, "offered_load": load, "budget_gb": budget / 1e9,
             "served": {k: served[k] for k in keep if k in served}, "plain": plain_sum}
 
 

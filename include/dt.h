@@ -80,9 +80,10 @@ extern "C" {
 #define DT_PART_LP 0         /* the initial blocks refined by lp_rounds rounds of size-constrained label
                                 propagation on the sample graph */
 #define DT_PART_MULTILEVEL 1 /* multilevel: heavy-edge matchings inside the initial blocks coarsen the
-                                graph level by level, then lp_rounds rounds of label propagation with
-                                vertex weights refine every level from the coarsest down (a coarse move
-                                moves a whole cluster of sample points) */
+                                graph level by level, then label propagation with vertex weights refines
+                                every level from the coarsest down, lp_rounds rounds on the sample graph
+                                and max(1, lp_rounds / 2) on each coarse level (a coarse move moves a
+                                whole cluster of sample points) */
 
 /* Edge weights of the sample graph (Table 1). */
 #define DT_WEIGHT_LOG 0
@@ -341,6 +342,72 @@ DT_API int dt_get_job_simplices(dt_ctx* ctx, uint64_t job, int32_t* out, int64_t
  * queued or running.  dt_destroy frees every job: it waits for the running
  * one and drops those still queued. */
 DT_API int dt_release_job(dt_ctx* ctx, uint64_t job);
+
+/* ---- continuous batching: one resident engine for a stream of jobs ---- */
+
+/* A stream keeps device buffers for `capacity` points (and their simplex
+ * arenas) on the context's GPU and triangulates many independent jobs of one
+ * dimension in the same insertion rounds.  Between rounds the engine returns
+ * to the host, which admits queued jobs into free room (each job an instance
+ * with its own insertion schedule) and extracts the jobs whose points are
+ * all inserted; a job that arrives while others run starts at the next round
+ * boundary.  Each job's result is exactly its DT (the same rows as a
+ * dt_triangulate of its points alone).  Not in the paper: a systems form of
+ * its per-partition triangulations (Alg. 1) for serving.
+ *
+ * dt_stream_open: dim 2 or 3; 16 <= capacity < 2^26 points; 1 <= max_jobs <=
+ * 1024 jobs resident at once.  One stream per context; it holds about
+ * (arena_factor x 48 + 100) bytes per point of capacity plus fixed scratch
+ * (dt_stream_get_info reports the total).  DT_E_NOMEM if the device cannot
+ * hold it. */
+DT_API int dt_stream_open(dt_ctx* ctx, int dim, int64_t capacity, int max_jobs);
+
+/* Queues a job: n points (n x dim float64, HOST memory, copied).  May be
+ * called from another host thread than dt_stream_run (the only call with
+ * that property).  *job receives its id.  A job needs n + 1 + ceil(32 /
+ * arena_factor) points of the capacity while it runs; DT_E_NOMEM if that
+ * exceeds the whole stream. */
+DT_API int dt_stream_submit(dt_ctx* ctx, const double* points, int64_t n, uint64_t* job);
+
+/* Runs up to `quanta` admission + round-loop passes: each admits queued jobs
+ * that fit (in arrival order; a job that does not fit yet lets smaller ones
+ * behind it pass), then runs insertion rounds until a job finishes, a new
+ * job is queued, or nothing is running; finished jobs are extracted.
+ * *pending (optional) receives the running + queued jobs.  A bad job
+ * (duplicate or non-finite points: DT_E_DUPLICATE / DT_E_ARG; fewer than
+ * dim + 1 or affinely dependent points: DT_E_ARG / DT_E_DEGENERATE) fails
+ * alone.  A device error fails every running job with its code and leaves
+ * the stream empty and usable; the call then returns that code. */
+DT_API int dt_stream_run(dt_ctx* ctx, int quanta, int* pending);
+
+/* Status of a job: 0 queued, 1 running, 2 done (rows in *count, optional),
+ * negative: the DT_E_* code it failed with.  DT_E_ARG for an unknown id. */
+DT_API int dt_stream_job(dt_ctx* ctx, uint64_t job, int* status, int64_t* count);
+
+/* A done job's simplices in dt_get_simplices' format (rows of dim + 1
+ * sorted input indices, rows sorted) into HOST memory; out NULL for a size
+ * query.  A failed job returns its code; DT_E_ARG otherwise. */
+DT_API int dt_stream_fetch(dt_ctx* ctx, uint64_t job, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Forgets a done or failed job (its rows are freed).  DT_E_ARG for an
+ * unknown, queued or running job. */
+DT_API int dt_stream_release(dt_ctx* ctx, uint64_t job);
+
+typedef struct dt_stream_info {
+  int64_t capacity;      /* points */
+  int64_t free_points;   /* points of the capacity not taken by running jobs */
+  int64_t device_bytes;  /* device memory the stream holds */
+  int32_t running, queued;
+  int64_t quanta;        /* round-loop passes so far */
+  int64_t rounds;        /* insertion rounds so far */
+  int64_t launches;      /* kernels the context has launched so far (every call) */
+} dt_stream_info;
+
+DT_API int dt_stream_get_info(dt_ctx* ctx, dt_stream_info* out);
+
+/* Frees the stream (waits for nothing: call it between dt_stream_run calls).
+ * dt_destroy closes an open stream too. */
+DT_API int dt_stream_close(dt_ctx* ctx);
 
 /* ---- step-level entry points (operate on caller buffers; host or device) ---- */
 

@@ -296,7 +296,7 @@ def contract(nbrs, vw, block: np.ndarray, mate: np.ndarray):
 
 def ml_partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: float = 0.05,
                  rounds: int = 16, init: str = "kd", sweeps: int = 4, max_levels: int = 12,
-                 trace: dict | None = None) -> np.ndarray:
+                 trace: dict | None = None, coarse_rounds: int | None = None) -> np.ndarray:
     """Multilevel size-constrained k-way partition of the sample graph (a
     multilevel scheme in the manner of KaHIP, which is not available),
     deterministic:
@@ -307,11 +307,12 @@ def ml_partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: floa
        repeated until a level keeps more than 95 % of its vertices (that
        level is dropped) or `max_levels` levels exist.  The coarse graphs
        inherit the blocks, so every level has the same block weights;
-    3. uncoarsening: from the coarsest level to the sample graph, `rounds`
-       rounds of `lp_refine` with the coarse vertex weights, then the
-       blocks are projected to the next finer level (a fine vertex takes its
-       coarse vertex's block).  Moving a coarse vertex moves a whole cluster
-       of sample vertices.
+    3. uncoarsening: from the coarsest level to the sample graph,
+       `coarse_rounds` (default max(1, rounds // 2)) rounds of `lp_refine`
+       with the coarse vertex weights on every coarse level and `rounds` on
+       the sample graph itself; after each level the blocks are projected to
+       the next finer level (a fine vertex takes its coarse vertex's block).
+       Moving a coarse vertex moves a whole cluster of sample vertices.
     trace (optional): filled with the per-level vertex counts, matchings,
     maps and blocks."""
     eta, D = PS.shape
@@ -335,9 +336,10 @@ def ml_partition(PS: np.ndarray, E: np.ndarray, w: np.ndarray, k: int, eps: floa
         blocks.append(cblock)
         cmaps.append(cmap)
     block = blocks[-1]
+    cr = max(1, rounds // 2) if coarse_rounds is None else coarse_rounds
     for lev in range(len(levels) - 1, -1, -1):
         nbrs, vw = levels[lev]
-        block = lp_refine(nbrs, vw, block, k, lmin, lmax, rounds)
+        block = lp_refine(nbrs, vw, block, k, lmin, lmax, rounds if lev == 0 else cr)
         if trace is not None:
             trace.setdefault("refined", []).append(block.copy())
         if lev > 0:

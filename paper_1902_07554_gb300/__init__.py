@@ -21,7 +21,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Triangulator", "DTError", "load_library", "declared_symbols", "Config", "Stats",
+__all__ = ["Triangulator", "Stream", "DTError", "load_library", "declared_symbols", "Config", "Stats",
            "DIVIDE_SAMPLE", "DIVIDE_KD", "PRIM_GRID", "PRIM_BBOX", "PRIM_POINTS", "INITS"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -81,6 +81,15 @@ class Stats(ctypes.Structure):
         return d
 
 
+class StreamInfo(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("free_points", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("running", ctypes.c_int32), ("queued", ctypes.c_int32), ("quanta", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class Validation(ctypes.Structure):
     """Result of the Delaunay certificate (dt_validate)."""
     _fields_ = [(name, ctypes.c_int64) for name in (
@@ -134,6 +143,14 @@ def load_library(build: bool = True):
         "dt_get_batch_status": ([p, p, i32], i32),
         "dt_select_sample_noalloc": ([i32, p, i64, i64, ctypes.c_uint64, p], i32),
         "dt_measure_fma_rate": ([i32, i32, i32, p], i32),
+        "dt_stream_open": ([p, i32, i64, i32], i32),
+        "dt_stream_submit": ([p, p, i64, p], i32),
+        "dt_stream_run": ([p, i32, p], i32),
+        "dt_stream_job": ([p, ctypes.c_uint64, p, p], i32),
+        "dt_stream_fetch": ([p, ctypes.c_uint64, p, i64, p], i32),
+        "dt_stream_release": ([p, ctypes.c_uint64], i32),
+        "dt_stream_get_info": ([p, p], i32),
+        "dt_stream_close": ([p], i32),
         "dt_get_neighbors": ([p, p, i64, p], i32),
         "dt_validate": ([p, p, i64, i32, p, i64, p], i32),
         "dt_submit": ([p, p, i64, i32, i32, dbl, p], i32),
@@ -405,3 +422,63 @@ class Triangulator:
         self._check(self.L.dt_partition_graph(self.ctx, _ptr(S), len(S), S.shape[1], _ptr(E), _ptr(w), len(E),
                                               k, float(eps), rounds, _ptr(out)))
         return out
+
+
+class Stream:
+    """Continuous batching on one context (dt_stream_*): jobs are submitted
+    from any thread and join the resident engine at the next round boundary;
+    one driver thread calls run().  Argument marshalling only."""
+
+    def __init__(self, tri: "Triangulator", dim: int, capacity: int, max_jobs: int = 256):
+        self.tri = tri
+        self.L = tri.L
+        self.dim = dim
+        tri._check(self.L.dt_stream_open(tri.ctx, dim, int(capacity), int(max_jobs)))
+
+    def submit(self, points) -> int:
+        a = np.ascontiguousarray(points, dtype=np.float64)
+        if a.ndim != 2 or a.shape[1] != self.dim:
+            raise ValueError(f"points must be (n, {self.dim})")
+        job = ctypes.c_uint64()
+        rc = self.L.dt_stream_submit(self.tri.ctx, _ptr(a), len(a), ctypes.byref(job))
+        if rc:
+            raise DTError(rc, "dt_stream_submit")
+        return job.value
+
+    def run(self, quanta: int = 1) -> int:
+        pending = ctypes.c_int()
+        self.tri._check(self.L.dt_stream_run(self.tri.ctx, quanta, ctypes.byref(pending)))
+        return pending.value
+
+    def status(self, job: int):
+        st, cnt = ctypes.c_int(), ctypes.c_int64()
+        rc = self.L.dt_stream_job(self.tri.ctx, job, ctypes.byref(st), ctypes.byref(cnt))
+        if rc:
+            raise DTError(rc, "dt_stream_job")
+        return st.value, cnt.value
+
+    def fetch(self, job: int) -> np.ndarray:
+        cnt = ctypes.c_int64()
+        rc = self.L.dt_stream_fetch(self.tri.ctx, job, None, 0, ctypes.byref(cnt))
+        if rc:
+            raise DTError(rc, "dt_stream_fetch")
+        out = np.empty((cnt.value, self.dim + 1), dtype=np.int32)
+        rc = self.L.dt_stream_fetch(self.tri.ctx, job, _ptr(out), cnt.value, ctypes.byref(cnt))
+        if rc:
+            raise DTError(rc, "dt_stream_fetch")
+        return out
+
+    def release(self, job: int):
+        rc = self.L.dt_stream_release(self.tri.ctx, job)
+        if rc:
+            raise DTError(rc, "dt_stream_release")
+
+    def info(self) -> dict:
+        out = StreamInfo()
+        self.tri._check(self.L.dt_stream_get_info(self.tri.ctx, ctypes.byref(out)))
+        return out.as_dict()
+
+    def close(self):
+        if self.tri.ctx:
+            self.L.dt_stream_close(self.tri.ctx)
+

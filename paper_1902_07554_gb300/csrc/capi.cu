@@ -95,6 +95,7 @@ extern "C" void dt_destroy(dt_ctx* c) {
   c->job_ctx = nullptr;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  dt_stream_cleanup(c);
   pool_free_all(c);
   if (c->status) cudaFree(c->status);
   if (c->status_host) cudaFreeHost(c->status_host);

@@ -7,7 +7,7 @@
 #include "common.cuh"
 #include "engine.cuh"
 
-namespace gdt { class JobQueue; }
+namespace gdt { class JobQueue; struct StreamState; }
 
 struct dt_ctx {
   int device = 0;
@@ -64,7 +64,12 @@ struct dt_ctx {
   // asynchronous jobs (dt_submit): a second context on the same device and its worker
   dt_ctx* job_ctx = nullptr;
   gdt::JobQueue* jobs = nullptr;
+  // continuous-batching stream (dt_stream_open), owned by the context
+  gdt::StreamState* stream_state = nullptr;
 };
+
+// Frees the context's stream, if one is open (stream_api.cu).
+void dt_stream_cleanup(dt_ctx* c);
 
 namespace gdt {
 

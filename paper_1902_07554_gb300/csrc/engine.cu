@@ -23,6 +23,18 @@ int pred_counters_engine(dt_ctx* c, unsigned long long* calls, int* range, bool 
   return 0;
 }
 
+int stream_setup_2d(dt_ctx* c, StreamState& st) { return stream_setup_t<2>(c, st); }
+int stream_admit_2d(dt_ctx* c, StreamState& st, StreamJob& j, const void* P) { return stream_admit_t<2>(c, st, j, P); }
+int stream_quantum_2d(dt_ctx* c, StreamState& st, int* yield) { return stream_quantum_t<2>(c, st, yield); }
+int stream_extract_2d(dt_ctx* c, StreamState& st, StreamJob& j) { return stream_extract_t<2>(c, st, j); }
+
+void stream_release_graph(StreamState& st) {
+  if (st.gx) cudaGraphExecDestroy(st.gx);
+  if (st.g) cudaGraphDestroy(st.g);
+  st.gx = nullptr;
+  st.g = nullptr;
+}
+
 int engine_run(dt_ctx* c, EngineRun& run, int dim, const void* pts, const int* gid, const int* pinst,
                int64_t npts, const std::vector<int64_t>& poff, const std::string& tag) {
   if (dim == 2) return engine_run_t<2>(c, run, pts, gid, pinst, npts, poff, tag);

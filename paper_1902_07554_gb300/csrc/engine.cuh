@@ -59,6 +59,7 @@ struct TriView {
   int ninst;
   unsigned long long* dbg;  // walk statistics (debug runs only; null otherwise)
   int rings;                // neighbour rings a nominee must hold the strongest pick in (1 or 2)
+  int* inst_kept;           // per instance: points still active after the round (continuous batching; else null)
   int walk_limit;           // steps of one location walk before DT_E_TIMEOUT
 };
 

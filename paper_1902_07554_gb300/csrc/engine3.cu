@@ -9,6 +9,11 @@ int engine_run_3d(dt_ctx* c, EngineRun& run, const void* pts, const int* gid, co
   return engine_run_t<3>(c, run, pts, gid, pinst, npts, poff, tag);
 }
 
+int stream_setup_3d(dt_ctx* c, StreamState& st) { return stream_setup_t<3>(c, st); }
+int stream_admit_3d(dt_ctx* c, StreamState& st, StreamJob& j, const void* P) { return stream_admit_t<3>(c, st, j, P); }
+int stream_quantum_3d(dt_ctx* c, StreamState& st, int* yield) { return stream_quantum_t<3>(c, st, yield); }
+int stream_extract_3d(dt_ctx* c, StreamState& st, StreamJob& j) { return stream_extract_t<3>(c, st, j); }
+
 int pred_counters_3d(dt_ctx* c, unsigned long long* calls, int* range, bool reset) {
   return pred_counters_local(c, calls, range, reset);
 }

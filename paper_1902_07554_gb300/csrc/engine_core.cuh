@@ -11,7 +11,9 @@
 
 #include "ctx.cuh"
 #include "bbox.cuh"
+#include "pipeline.cuh"
 #include "sort.cuh"
+#include "stream.cuh"
 
 namespace gdt {
 
@@ -89,16 +91,6 @@ __device__ __forceinline__ void hint_cells(const TriView<D>& T, int p, int& fine
   }
   fine = d[3] + id;
   coarse = d[4] + id2;
-}
-
-template <int D>
-__device__ __forceinline__ int inst_of_slot_e(const TriView<D>& T, int s) {
-  int lo = 0, hi = T.ninst - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (T.toff[mid] <= s) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 template <int D>
@@ -806,6 +798,7 @@ __device__ __forceinline__ void reloc_check_warp(const TriView<D>& T, const int*
   }
   warp_append(act_out, nact_out, keep, p);
   warp_append(walk, nwalk, walker, p);
+  if (T.inst_kept && keep) atomicAdd(&T.inst_kept[T.pinst[p]], 1);
   if (T.prof) {
     // act 4, state 1, loc 4, slot word 4, pick 8, output 4
     unsigned long long b = idx < nact ? 25 : 0;
@@ -835,6 +828,39 @@ __global__ void k_reloc_check(TriView<D> T, const int* act, const int* nact_p, i
 // to the active list.
 // Activation of the 32 dormant points from `base` of list (one warp):
 // locate each from its hint cell (or its parked simplex) and pick.
+// Is simplex slot h inside instance i's arena?
+template <int D>
+__device__ __forceinline__ bool in_instance(const TriView<D>& T, int h, int i) {
+  return slot_ok(T, h) && h >= T.toff[i] && h < T.tend[i];
+}
+
+// Locates dormant point p from its hint cell (or its parked simplex) and
+// makes its pick for next_round; false when the walk gave up.
+template <int D>
+__device__ __forceinline__ bool activate_point(const TriView<D>& T, int p, unsigned next_round) {
+  int s = T.loc[p];
+  if (T.hint) {
+    int f, g;
+    hint_cells(T, p, f, g);
+    const int i = T.pinst[p];
+    int h = T.hint[f];
+    if (!in_instance(T, h, i)) h = T.hint2[g];
+    if (in_instance(T, h, i)) s = h;
+  }
+  for (int hop = 0; hop < T.walk_limit && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
+    s = nb_simplex(*comp_ptr(T.tn, s, 0));
+  int steps = 0;
+  int r = walk_to(T, s, p, T.walk_limit, &steps);
+  if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
+  if (r < 0) {
+    set_error(T.st, DT_E_TIMEOUT, 4);
+    return false;
+  }
+  T.loc[p] = r;
+  atomicMax(&T.claimC[r], mkkey(next_round, p));
+  return true;
+}
+
 template <int D>
 __device__ __forceinline__ void activate_warp(const TriView<D>& T, const int* list, int m, int* act, int* nact,
                                               unsigned next_round, int64_t base) {
@@ -843,26 +869,7 @@ __device__ __forceinline__ void activate_warp(const TriView<D>& T, const int* li
   int p = -1;
   if (idx < m) {
     p = list[idx];
-    int s = T.loc[p];
-    if (T.hint) {
-      int f, g;
-      hint_cells(T, p, f, g);
-      int h = T.hint[f];
-      if (!(slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p])) h = T.hint2[g];
-      if (slot_ok(T, h) && inst_of_slot_e(T, h) == T.pinst[p]) s = h;
-    }
-    for (int hop = 0; hop < T.walk_limit && slot_ok(T, s) && *comp_ptr(T.tv, s, 0) == DEAD; hop++)
-      s = nb_simplex(*comp_ptr(T.tn, s, 0));
-    int steps = 0;
-    int r = walk_to(T, s, p, T.walk_limit, &steps);
-    if (T.dbg) { atomicAdd(&T.dbg[2], (unsigned long long)steps); atomicMax(&T.dbg[3], (unsigned long long)steps); }
-    if (r < 0) {
-      set_error(T.st, DT_E_TIMEOUT, 4);
-    } else {
-      T.loc[p] = r;
-      atomicMax(&T.claimC[r], mkkey(next_round, p));
-      ok = true;
-    }
+    ok = activate_point(T, p, next_round);
   }
   warp_append(act, nact, ok, p);
 }
@@ -1815,6 +1822,593 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
     return 0;
   }
   return set_err(c, DT_E_OVERFLOW, "simplex arena overflow after retries");
+}
+
+
+// ---------------------------------------------------------------- continuous batching
+// The stream engine (stream.cuh): the same round kernels over the resident
+// instances, with an activation schedule per instance and a round loop that
+// yields to the host when an instance has finished or jobs are waiting.
+
+// Activation plan of the next round, one thread per instance (the whole CTA
+// calls it): every running instance activates its next level(s) once its
+// active set has drained to last_batch / drain; seg[0..J) receives each
+// instance's range start in llist, seg[J..2J] the exclusive prefix of the
+// range lengths.
+static __device__ void stream_plan(EngCtl& C, SlotState* ss, int J, int* seg, int* cnt, int drain) {
+  __shared__ int s_len[STREAM_MAX_JOBS];
+  for (int t = threadIdx.x; t < J; t += blockDim.x) {
+    SlotState& q = ss[t];
+    int len = 0, lo = -1, hi = -1;
+    if (q.status == 1) {
+      int nact = q.nact;
+      while (q.next_level >= 0 && nact <= q.last_batch / drain) {
+        const int l = q.next_level;
+        const int m = q.loff[l + 1] - q.loff[l];
+        if (m > 0) {
+          if (hi < 0) hi = q.loff[l + 1];
+          lo = q.loff[l];
+          nact += m;
+          q.last_batch = nact;
+        }
+        q.next_level--;
+      }
+      q.nact = nact;
+      if (lo >= 0) len = hi - lo;
+    }
+    seg[t] = lo;
+    s_len[t] = len;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < J; t++) { seg[J + t] = run; run += s_len[t]; }
+    seg[2 * J] = run;
+    C.act_lo = 0;
+    C.act_n = run;
+    C.activated = run;
+    if (cnt[0] + run > 0) C.round++;
+    cnt[1] = cnt[2] = cnt[3] = cnt[4] = cnt[5] = 0;
+    for (int b = 0; b < NBUCKET; b++) cnt[8 + b] = 0;
+  }
+  __syncthreads();
+}
+
+static __global__ void k_stream_begin(EngCtl* ctl, SlotState* ss, int J, int* seg, int* cnt, int drain) {
+  stream_plan(*ctl, ss, J, seg, cnt, drain);
+}
+
+// End of a round: per-instance survivors, finished instances, the yield
+// decision, then the plan of the next round.
+static __global__ void k_stream_step(EngCtl* ctl, SlotState* ss, int J, int* seg, int* cnt, int* kept,
+                                     const DevStatus* st, const volatile int* admit, int drain,
+                                     cudaGraphConditionalHandle handle) {
+  pdl_enter();
+  __shared__ int s_fin, s_live;
+  EngCtl& C = *ctl;
+  if (threadIdx.x == 0) {
+    s_fin = 0;
+    s_live = 0;
+    const int had = cnt[0];
+    const int nnew = cnt[1];
+    cnt[0] = nnew;
+    cnt[1] = 0;
+    int* t = C.ain;
+    C.ain = C.aout;
+    C.aout = t;
+    if (C.done == 0) {
+      if (st->error) C.done = 2;
+      else if (had > 0 && cnt[3] == 0 && ++C.stalled >= 4) C.done = 3;
+      else if (cnt[3] > 0) C.stalled = 0;
+    }
+    C.last_nact = nnew;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < J; t += blockDim.x) {
+    SlotState& q = ss[t];
+    if (q.status == 1) {
+      q.nact = kept[t];
+      if (q.nact == 0 && q.next_level < 0) {
+        q.status = 2;
+        atomicAdd(&s_fin, 1);
+      } else {
+        atomicAdd(&s_live, 1);
+      }
+    }
+    kept[t] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && C.done == 0) {
+    if (s_fin > 0 || *admit) C.done = 5;        // yield: extract / admit at this round boundary
+    else if (s_live == 0) C.done = 1;
+  }
+  __syncthreads();
+  if (C.done == 0) stream_plan(C, ss, J, seg, cnt, drain);
+  if (threadIdx.x == 0) cudaGraphSetConditional(handle, C.done == 0 ? 1u : 0u);
+}
+
+// Activation over the per-instance ranges of the plan.
+template <int D>
+__global__ void __launch_bounds__(128, 8) k_stream_activate(TriView<D> T, const int* llist, const int* seg, int J,
+                                                         int* nact, const EngCtl* ctl) {
+  pdl_enter();
+  if (ctl->done) return;
+  const int m = ctl->act_n;
+  int* act = ctl->ain;
+  const unsigned next_round = ctl->round;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < m;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = base + (threadIdx.x & 31);
+    bool ok = false;
+    int p = -1;
+    if (idx < m) {
+      int lo = 0, hi = J - 1;                   // the last instance whose range starts at or before idx
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg[J + mid] <= idx) lo = mid; else hi = mid - 1;
+      }
+      p = llist[seg[lo] + (int)(idx - seg[J + lo])];
+      ok = activate_point(T, p, next_round);
+    }
+    warp_append(act, nact, ok, p);
+  }
+}
+
+// Points of a newly admitted instance: every point waits on the initial
+// simplex; those of the first levels are located in it, pick for
+// next_round and join the active list.
+template <int D>
+__global__ void k_stream_locate(TriView<D> T, int slot, int64_t p0, int64_t n, const int* level, int first_level,
+                                int* act, int* nact, SlotState* ss, unsigned next_round) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool active = false;
+  const int p = (int)(p0 + q);
+  if (q < n && T.state[p] == 0) {
+    const int s0 = T.toff[slot];
+    T.loc[p] = s0;
+    if (level[p] >= first_level) {
+      const int4 vv = T.tv[s0];
+      int loc = s0;
+      for (int j = 0; j <= D; j++) {
+        int4 t = vv;
+        set4(t, j, p);
+        if (orient_tuple(T, t) < 0) { loc = nb_simplex(get4(T.tn[s0], j)); break; }
+      }
+      T.loc[p] = loc;
+      atomicMax(&T.claimC[loc], mkkey(next_round, p));
+      active = true;
+      atomicAdd(&ss[slot].nact, 1);
+      atomicAdd(&ss[slot].last_batch, 1);
+    }
+  }
+  warp_append(act, nact, active, p);
+}
+
+// The level lists of an admitted instance: point p0 + q goes to its level's
+// range at its rank there.
+static __global__ void k_stream_scatter_levels(const int* level, const int* rank, const SlotState* ss, int slot, int64_t p0,
+                                        int64_t n, int* llist) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int l = level[p0 + q];
+  if (l >= 0) llist[ss[slot].loff[l] + rank[p0 + q]] = (int)(p0 + q);
+}
+
+static __global__ void k_stream_fill(int* a, int64_t n, int v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+static __global__ void k_stream_iota(int* a, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (int)i;
+}
+
+static __device__ __forceinline__ void cswap(int& a, int& b) {
+  if (b < a) { const int t = a; a = b; b = t; }
+}
+
+// Finite live simplices of one instance's arena range as rows of local
+// indices, each sorted.
+template <int D>
+__global__ void k_stream_rows(const int4* tv, int a, int b, const int* gid, int4* rows, int* nrows) {
+  const int s = a + blockIdx.x * blockDim.x + threadIdx.x;
+  bool take = false;
+  int4 r = make_int4(0, 0, 0, 0);
+  if (s < b) {
+    const int4 v = tv[s];
+    if (v.x >= 0 && v.y >= 0 && v.z >= 0 && (D == 2 || v.w >= 0)) {
+      take = true;
+      int x = gid[v.x], y = gid[v.y], z = gid[v.z], w = D == 3 ? gid[v.w] : 0x7fffffff;
+      cswap(x, y); cswap(z, w); cswap(x, z); cswap(y, w); cswap(y, z);   // a sorting network (w = max for 2D)
+      r = make_int4(x, y, z, w);
+    }
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, take);
+  if (!mask) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(nrows, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (take) rows[base + __popc(mask & ((1u << lane) - 1))] = r;
+}
+
+template <int D>
+static TriView<D> stream_view(dt_ctx* c, StreamState& st) {
+  TriView<D> T;
+  memset(&T, 0, sizeof(T));
+  T.pts = (const typename PT<D>::T*)st.pts;
+  T.xs = st.xs;
+  T.gid = st.gid;
+  T.pinst = st.pinst;
+  T.tv = st.tv;
+  T.tn = st.tn;
+  T.claimA = st.claimA;
+  T.claimC = st.claimC;
+  T.tcount = st.tcount;
+  T.tend = st.tend;
+  T.loc = st.loc;
+  T.state = st.state;
+  T.st = c->status;
+  T.nslots = (int)(st.arena_factor * st.cap + 64);
+  T.npts = (int)st.cap;
+  T.hint = st.hint;
+  T.hint2 = st.hint2;
+  T.glo = st.glo;
+  T.gdim = st.gdim;
+  T.toff = st.toff;
+  T.ninst = st.max_jobs;
+  T.rings = c->cfg.nominate_rings > 1 ? 2 : 1;
+  T.walk_limit = c->cfg.walk_limit > 0 ? c->cfg.walk_limit : (1 << 16);
+  T.inst_kept = st.kept;
+  return T;
+}
+
+// Allocates the stream's device buffers for st.cap points and st.max_jobs
+// instances (held until the stream closes) and resets its round state.
+template <int D>
+static int stream_setup_t(dt_ctx* c, StreamState& st) {
+  cudaStream_t s = c->stream;
+  const int64_t cap = st.cap, J = st.max_jobs, A = st.arena_factor * cap + 64;
+  bool ok = true;
+  auto get = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (!ok || cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) { cudaGetLastError(); ok = false; return nullptr; }
+    st.owned.push_back(p);
+    st.bytes += std::max<size_t>(bytes, 16);
+    return p;
+  };
+  if (!st.pts) {                       // first call: allocate; later calls only reset
+  st.pts = get(sizeof(typename PT<D>::T) * cap);
+  st.gid = (int*)get(4 * cap); st.pinst = (int*)get(4 * cap); st.loc = (int*)get(4 * cap);
+  st.level = (int*)get(4 * cap); st.lrank = (int*)get(4 * cap); st.lsize = (int*)get(4 * (STREAM_NLEV + 1));
+  st.state = (unsigned char*)get(cap); st.xs = (float4*)get(16 * cap);
+  st.llist = (int*)get(4 * cap); st.act0 = (int*)get(4 * cap); st.act1 = (int*)get(4 * cap); st.walk = (int*)get(4 * cap);
+  st.nom = (int*)get(4 * (size_t)NBUCKET * st.cap_cand);
+  st.tv = (int4*)get(16 * A); st.tn = (int4*)get(16 * A);
+  st.claimA = (unsigned long long*)get(8 * A); st.claimC = (unsigned long long*)get(8 * A);
+  st.toff = (int*)get(4 * J); st.tend = (int*)get(4 * J); st.tcount = (int*)get(4 * J); st.inst_status = (int*)get(4 * J);
+  st.xo = (double*)get(8 * 4 * J); st.glo = (double*)get(8 * 6 * J); st.gdim = (int*)get(4 * 5 * J);
+  st.hint = (int*)get(4 * cap); st.hint2 = (int*)get(4 * cap);
+  st.ss = (SlotState*)get(sizeof(SlotState) * J); st.seg = (int*)get(4 * (2 * J + 1)); st.kept = (int*)get(4 * J);
+  st.cnt = (int*)get(64); st.ctl = get(sizeof(EngCtl));
+  CandScratch& S = st.S;
+  memset(&S, 0, sizeof(S));
+  S.cap = (int)st.cap_cand;
+  S.capC = st.capC;
+  S.capB = st.capB;
+  S.cand = (int*)get(4 * st.cap_cand); S.meta = (int4*)get(16 * st.cap_cand);
+  S.cav = (int*)get(4 * st.cap_cand * st.capC); S.bnd = (int*)get(4 * st.cap_cand * st.capB);
+  S.outer = (int*)get(4 * st.cap_cand * st.capB);
+  S.count = st.cnt + 2;
+  S.capCbig = BIG_C; S.capBbig = BIG_B;
+  S.bigcav = (int*)get(4 * (size_t)BIGCAP * BIG_C); S.bigbnd = (int*)get(4 * (size_t)BIGCAP * BIG_B);
+  S.bigout = (int*)get(4 * (size_t)BIGCAP * BIG_B); S.biglist = (int*)get(4 * (size_t)BIGCAP);
+  S.nbig = st.cnt + 5;
+  if (!ok) return set_err(c, DT_E_NOMEM, "stream buffers");
+  }
+  CUDA_OK(cudaMemsetAsync(st.toff, 0, 4 * J, s));
+  CUDA_OK(cudaMemsetAsync(st.tend, 0, 4 * J, s));
+  CUDA_OK(cudaMemsetAsync(st.claimA, 0, 8 * (size_t)A, s));
+  CUDA_OK(cudaMemsetAsync(st.claimC, 0, 8 * (size_t)A, s));
+  CUDA_OK(cudaMemsetAsync(st.ss, 0, sizeof(SlotState) * st.max_jobs, s));
+  CUDA_OK(cudaMemsetAsync(st.kept, 0, 4 * st.max_jobs, s));
+  CUDA_OK(cudaMemsetAsync(st.cnt, 0, 64, s));
+  CUDA_OK(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+  EngCtl h0;
+  memset(&h0, 0, sizeof(h0));
+  h0.ain = st.act0;
+  h0.aout = st.act1;
+  h0.next_level = -1;
+  h0.small_max = -1;
+  h0.drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
+  h0.round_limit = 0x7fffffff;
+  CUDA_OK(cudaMemcpyAsync(st.ctl, &h0, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  st.round = 0;
+  return 0;
+}
+
+// Sets up job j in its range [p0, p0 + n) and instance slot: points (already
+// in the engine's layout at P, staged and checked), FP32 copies, hint grid,
+// initial simplex, level lists, first batch.
+template <int D>
+static int stream_admit_t(dt_ctx* c, StreamState& st, StreamJob& j, const void* P) {
+  using PTT = typename PT<D>::T;
+  cudaStream_t s = c->stream;
+  const int slot = j.slot;
+  const int64_t p0 = j.p0, n = j.n;
+  const unsigned g = (unsigned)ceil_div<int64_t>(std::max<int64_t>(n, 1), 256);
+  PTT* pts = (PTT*)st.pts + p0;
+  CUDA_OK(cudaMemcpyAsync(pts, P, sizeof(PTT) * n, cudaMemcpyDeviceToDevice, s));
+  k_stream_iota<<<g, 256, (++c->launches, 0), s>>>(st.gid + p0, n);
+  k_stream_fill<<<g, 256, (++c->launches, 0), s>>>(st.pinst + p0, n, slot);
+  CUDA_OK(cudaMemsetAsync(st.state + p0, 0, (size_t)n, s));
+  // bounding box: FP32 origin and error bound, hint grid of about n / 4 cells
+  unsigned long long* ub = (unsigned long long*)pool_get(c, "stream.box", 8 * 6);
+  if (!ub) return set_err(c, DT_E_NOMEM, "stream box");
+  k_box_init<<<1, 32, (++c->launches, 0), s>>>(ub, 1);
+  k_box_reduce<D><<<box_grid(n), 256, (++c->launches, 0), s>>>(pts, nullptr, n, ub);
+  unsigned long long hu[6];
+  CUDA_OK(cudaMemcpyAsync(hu, ub, 48, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  double xo[4] = {0, 0, 0, 0}, glo[6] = {0, 0, 0, 0, 0, 0};
+  int gd[5] = {1, 1, 1, (int)p0, (int)p0};
+  double R = 0.0, lo[3] = {0, 0, 0}, ext[3] = {0, 0, 0}, vol = 1.0;
+  int nd = 0;
+  for (int cc = 0; cc < D; cc++) {
+    lo[cc] = host_from_orderable(hu[cc]);
+    const double hi = host_from_orderable(hu[3 + cc]);
+    const double o = 0.5 * lo[cc] + 0.5 * hi;
+    xo[cc] = o;
+    R = std::max(R, std::max(hi - o, o - lo[cc]));
+    ext[cc] = hi > lo[cc] ? hi - lo[cc] : 0.0;
+    if (ext[cc] > 0) { vol *= ext[cc]; nd++; }
+  }
+  const double eta = 2.02 * (std::ldexp(1.0, -24) + std::ldexp(1.0, -52)) * R * (1.0 + 1e-9);
+  float ef = (float)eta;
+  if (!((double)ef >= eta)) ef = std::nextafter(ef, INFINITY);
+  xo[3] = (double)ef;
+  // fine cells: at most n (the job's share of the cell arrays), about n / 4
+  double side = nd ? std::pow(vol / std::max(1.0, (double)n / 4.0), 1.0 / nd) : 1.0;
+  int64_t cells = 1;
+  for (int tries = 0; tries < 200; tries++) {
+    cells = 1;
+    for (int cc = 0; cc < 3; cc++) {
+      int d = 1;
+      if (cc < D && ext[cc] > 0 && side > 0) d = (int)std::min(1024.0, std::max(1.0, std::ceil(ext[cc] / side)));
+      gd[cc] = d;
+      cells *= d;
+    }
+    if (cells <= std::max<int64_t>(n, 1)) break;
+    side *= 1.1;
+  }
+  for (int cc = 0; cc < 3; cc++) {
+    glo[cc] = cc < D ? lo[cc] : 0.0;
+    glo[3 + cc] = (cc < D && ext[cc] > 0) ? gd[cc] / ext[cc] : 0.0;
+  }
+  int64_t cells2 = 1;
+  for (int cc = 0; cc < 3; cc++) cells2 *= (gd[cc] + 3) >> 2;
+  CUDA_OK(cudaMemcpyAsync(st.xo + 4 * slot, xo, 32, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(st.glo + 6 * slot, glo, 48, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(st.gdim + 5 * slot, gd, 20, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemsetAsync(st.hint + p0, 0xff, 4 * (size_t)cells, s));
+  CUDA_OK(cudaMemsetAsync(st.hint2 + p0, 0xff, 4 * (size_t)cells2, s));
+  k_make_x32<D><<<g, 256, (++c->launches, 0), s>>>(pts, st.pinst + p0, n, st.xo, st.xs + p0);
+  // arena and initial simplex (k_init on a view whose instance 0 is this slot)
+  const int a0 = (int)(st.arena_factor * p0);
+  const int a1 = (int)(st.arena_factor * (p0 + n) + 32);
+  const int bounds[2] = {a0, a1};
+  CUDA_OK(cudaMemcpyAsync(st.toff + slot, &bounds[0], 4, cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemcpyAsync(st.tend + slot, &bounds[1], 4, cudaMemcpyHostToDevice, s));
+  long long* dpoff = (long long*)pool_get(c, "stream.poff", 16);
+  if (!dpoff) return set_err(c, DT_E_NOMEM, "stream offsets");
+  const long long hpoff[2] = {(long long)p0, (long long)(p0 + n)};
+  CUDA_OK(cudaMemcpyAsync(dpoff, hpoff, 16, cudaMemcpyHostToDevice, s));
+  TriView<D> T = stream_view<D>(c, st);
+  TriView<D> Ti = T;
+  Ti.tcount = st.tcount + slot;
+  k_init<D><<<1, 32, (++c->launches, 0), s>>>(Ti, 1, dpoff, st.toff + slot, st.inst_status + slot);
+  int istat = 0;
+  CUDA_OK(cudaMemcpyAsync(&istat, st.inst_status + slot, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (istat != 0) {
+    j.status = istat == 1 ? DT_E_DEGENERATE : DT_E_ARG;
+    return 0;
+  }
+  // activation levels and the instance's level lists
+  const double growth = c->cfg.brio_growth > 100 ? c->cfg.brio_growth / 100.0 : 1.5;
+  TriView<D> Tl = T;
+  Tl.pinst = st.pinst + p0;
+  Tl.state = st.state + p0;
+  Tl.gid = st.gid + p0;
+  k_levels<D><<<g, 256, (++c->launches, 0), s>>>(Tl, n, st.inst_status, st.level + p0,
+                                                 (float)(1.0 / std::log2(growth)));
+  int rc = group_rank(c, st.level + p0, n, st.lrank + p0, st.lsize, STREAM_NLEV);
+  if (rc) return rc;
+  int hs[STREAM_NLEV];
+  CUDA_OK(cudaMemcpyAsync(hs, st.lsize, 4 * STREAM_NLEV, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  SlotState q;
+  memset(&q, 0, sizeof(q));
+  q.loff[0] = (int)p0;
+  for (int l = 0; l < STREAM_NLEV; l++) q.loff[l + 1] = q.loff[l] + hs[l];
+  const int fb = c->cfg.first_batch > 0 ? c->cfg.first_batch : 32;
+  int first_level = STREAM_NLEV - 1;
+  while (first_level > 0 && q.loff[STREAM_NLEV] - q.loff[first_level] < fb) first_level--;
+  q.status = 1;
+  q.next_level = first_level - 1;
+  CUDA_OK(cudaMemcpyAsync(st.ss + slot, &q, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+  k_stream_scatter_levels<<<g, 256, (++c->launches, 0), s>>>(st.level, st.lrank, st.ss, slot, p0, n, st.llist);
+  EngCtl h;
+  CUDA_OK(cudaMemcpyAsync(&h, st.ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  k_stream_locate<D><<<g, 256, (++c->launches, 0), s>>>(T, slot, p0, n, st.level, first_level, h.ain, st.cnt + 0,
+                                                        st.ss, h.round + 1);
+  j.status = 1;
+  return 0;
+}
+
+// Builds the round graph of the stream: the same body as the engine's
+// graph, with the per-instance activation and round end.
+template <int D>
+static int stream_graph(dt_ctx* c, StreamState& st, cudaGraphConditionalHandle* hc_out) {
+  cudaStream_t cs = capture_stream(c);
+  if (!cs) return set_err(c, DT_E_NOMEM, "capture stream");
+  stream_release_graph(st);
+  TriView<D> T = stream_view<D>(c, st);
+  const int capCand = (int)st.cap_cand;
+  const int J = st.max_jobs;
+  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div<int64_t>(st.cap, 256), 152 * 8);
+  const unsigned gr = (unsigned)std::min<int64_t>(ceil_div<int64_t>(st.cap, 128), 152 * 16);
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
+  const int drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
+  const unsigned tb = (unsigned)std::min(1024, std::max(32, ((J + 31) / 32) * 32));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  cudaGraphConditionalHandle hc = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const bool pdl = st.graph_pdl;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    auto cfg = [&](unsigned grid, unsigned block) {
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(grid);
+      lc.blockDim = dim3(block);
+      lc.stream = cs;
+      lc.attrs = pdl ? at : nullptr;
+      lc.numAttrs = pdl ? 1 : 0;
+      return lc;
+    };
+    EngCtl* ctl = (EngCtl*)st.ctl;
+    int* cnt = st.cnt;
+    cudaLaunchConfig_t l1 = cfg(gr, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128), l5 = cfg(gn, 256),
+                       l6 = cfg(gr, 128), l7 = cfg(1, tb), l8 = cfg(BIGCAP / 4, 128);
+    l1.numAttrs = 0;
+    cudaLaunchKernelEx(&l1, k_stream_activate<D>, T, (const int*)st.llist, (const int*)st.seg, J, cnt + 0,
+                       (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, st.nom, cnt + 2, cnt + 8,
+                       capCand, (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l3, k_cavity_w<D>, T, (const int*)st.nom, (const int*)(cnt + 2), 0u, st.S,
+                       (const int*)(cnt + 8), (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l8, k_cavity_big<D>, T, 0u, st.S, (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l4, k_insert_w<D>, T, 0u, st.S, (const int*)(cnt + 2), cnt + 3, (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l5, k_reloc_check<D>, T, (const int*)nullptr, (const int*)(cnt + 0), (int*)nullptr, cnt + 1,
+                       st.walk, cnt + 4, 0u, (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l6, k_reloc_walk<D>, T, (const int*)st.walk, (const int*)(cnt + 4), 0u, (const EngCtl*)ctl);
+    cudaLaunchKernelEx(&l7, k_stream_step, ctl, st.ss, J, st.seg, cnt, st.kept, (const DevStatus*)c->status,
+                       (const volatile int*)st.admit_dev, drain, hc);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+  }
+  cudaGraphExec_t gx = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (gx) cudaGraphExecDestroy(gx);
+    if (g) cudaGraphDestroy(g);
+    if (st.graph_pdl) {   // programmatic edges refused: without them
+      st.graph_pdl = false;
+      return stream_graph<D>(c, st, hc_out);
+    }
+    return set_err(c, gdt_cuda_fail(e, "stream graph", __FILE__, __LINE__), "stream graph");
+  }
+  st.g = g;
+  st.gx = gx;
+  *hc_out = hc;
+  return 0;
+}
+
+// One quantum: plan, then rounds until an instance finishes, jobs wait, the
+// active set empties, or an error.  *yield: the loop's end code.
+template <int D>
+static int stream_quantum_t(dt_ctx* c, StreamState& st, int* yield) {
+  cudaStream_t s = c->stream;
+  for (int grow = 0;; grow++) {
+    if (!st.gx) {
+      cudaGraphConditionalHandle hc;
+      int rc = stream_graph<D>(c, st, &hc);
+      if (rc) return rc;
+    }
+    const int drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
+    const unsigned tb = (unsigned)std::min(1024, std::max(32, ((st.max_jobs + 31) / 32) * 32));
+    // the graph's first round: clear the end code, plan
+    EngCtl h;
+    CUDA_OK(cudaMemcpyAsync(&h, st.ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    const unsigned r0 = h.round;
+    h.done = 0;
+    h.stalled = 0;
+    CUDA_OK(cudaMemcpyAsync(st.ctl, &h, sizeof(EngCtl), cudaMemcpyHostToDevice, s));
+    k_stream_begin<<<1, tb, 0, s>>>((EngCtl*)st.ctl, st.ss, st.max_jobs, st.seg, st.cnt, drain);
+    cudaError_t e = cudaGraphLaunch(st.gx, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_err(c, gdt_cuda_fail(e, "stream rounds", __FILE__, __LINE__), "stream rounds");
+    CUDA_OK(cudaMemcpyAsync(&h, st.ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    st.quanta++;
+    st.rounds_run += h.round - r0;
+    c->launches += 2 + 8 * (int64_t)(h.round - r0 + 1);
+    st.round = h.round;
+    if (h.done == 3 && c->status_host->overflow_cav && grow < 6) {
+      // cavities outgrew their scratch: twice the room, a new graph, same state
+      CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));
+      st.capC *= 2;
+      st.capB *= 2;
+      st.S.capC = st.capC;
+      st.S.capB = st.capB;
+      st.S.cav = (int*)pool_get(c, "stream.cav", 4 * (size_t)st.cap_cand * st.capC);
+      st.S.bnd = (int*)pool_get(c, "stream.bnd", 4 * (size_t)st.cap_cand * st.capB);
+      st.S.outer = (int*)pool_get(c, "stream.outer", 4 * (size_t)st.cap_cand * st.capB);   // pool-owned from now on
+      if (!st.S.cav || !st.S.bnd || !st.S.outer) return set_err(c, DT_E_NOMEM, "stream cavity scratch");
+      stream_release_graph(st);
+      continue;
+    }
+    *yield = h.done;
+    if (h.done == 2) return check_status(c, "stream round");
+    if (h.done == 3) return set_err(c, DT_E_INTERNAL, "stream rounds made no progress");
+    return 0;
+  }
+}
+
+template <int D>
+static int stream_extract_t(dt_ctx* c, StreamState& st, StreamJob& j) {
+  cudaStream_t s = c->stream;
+  int ab[2] = {0, 0};
+  CUDA_OK(cudaMemcpyAsync(&ab[0], st.toff + j.slot, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaMemcpyAsync(&ab[1], st.tcount + j.slot, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  const int64_t used = std::max(0, ab[1] - ab[0]);
+  int4* rows = (int4*)pool_get(c, "stream.rows", 16 * std::max<int64_t>(used, 16));
+  int* cnt = (int*)pool_get(c, "stream.rowcnt", 16);
+  if (!rows || !cnt) return set_err(c, DT_E_NOMEM, "stream rows");
+  CUDA_OK(cudaMemsetAsync(cnt, 0, 4, s));
+  if (used > 0)
+    k_stream_rows<D><<<(unsigned)ceil_div<int64_t>(used, 256), 256, (++c->launches, 0), s>>>(st.tv, ab[0], ab[1], st.gid,
+                                                                                             rows, cnt);
+  int nrows = 0;
+  CUDA_OK(cudaMemcpyAsync(&nrows, cnt, 4, cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  int32_t* out = nullptr;
+  int64_t nout = 0;
+  int rc = canonicalize_rows(c, D, rows, nrows, std::max<int64_t>(j.n, 1), &out, &nout, "stream.canon");
+  if (rc) return rc;
+  j.rows.resize((size_t)nout * (D + 1));
+  if (nout) CUDA_OK(cudaMemcpyAsync(j.rows.data(), out, 4 * (size_t)nout * (D + 1), cudaMemcpyDeviceToHost, s));
+  CUDA_OK(cudaStreamSynchronize(s));
+  return 0;
 }
 
 }  // namespace gdt

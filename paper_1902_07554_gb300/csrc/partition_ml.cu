@@ -349,8 +349,9 @@ int partition_multilevel(dt_ctx* c, const SampleGraph& G, int k, double eps, int
     if ((double)cg.n > 0.95 * (double)g.n) break;
     lv.push_back(cg);
   }
+  // rounds on the sample graph, half as many (at least one) on every coarse level
   for (int l = (int)lv.size() - 1; l >= 0; l--) {
-    int rc = ml_lp(c, lv[l], k, lmin, lmax, rounds, "ml.lp" + std::to_string(l));
+    int rc = ml_lp(c, lv[l], k, lmin, lmax, l == 0 ? rounds : std::max(1, rounds / 2), "ml.lp" + std::to_string(l));
     if (rc) return rc;
     if (l > 0)
       k_ml_project<<<grid_of(lv[l - 1].n), 256, (++c->launches, 0), s>>>(lv[l - 1].n, lv[l - 1].cmap, lv[l].block,

@@ -1,18 +1,20 @@
 """Continuous-batching server for triangulation jobs on one GPU.
 
-Jobs (point sets) arrive over time.  A job is admitted when a worker is free
-and its estimated device memory fits the remaining budget; small jobs that are
-waiting together are packed into one batched call (dt_triangulate_batch),
-large ones run the divide-and-conquer path.  Every worker owns a library
-context with its own CUDA stream, so admitted work from different workers
-overlaps on the device while new requests keep arriving.  Latency is measured
-from a job's arrival to the moment its simplices are back on the host.
+Jobs (point sets) arrive over time.  The server keeps ONE resident insertion
+engine (the library's stream, dt_stream_*): device buffers for `capacity`
+points, sized from a device-memory budget with a per-point cost measured from
+the library itself (`calibrate`).  An arriving job is queued at once; the
+engine, which runs every admitted job's insertion rounds together, returns
+to the host at the next round boundary, admits the queued jobs that fit into
+free room, and hands back each job as soon as its last point is inserted.
+Small jobs therefore never wait for a large one to finish, and all jobs in
+flight share every round's launches.  Latency is measured from a job's
+arrival to the moment its simplices are on the host.
 
 Everything runs through the library's C ABI; Python only schedules.
 """
 from __future__ import annotations
 
-import heapq
 import math
 import threading
 import time
@@ -20,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Triangulator
+from . import Stream, Triangulator
 
 
 @dataclass(order=True)
@@ -28,7 +30,7 @@ class Job:
     arrival: float
     jid: int = field(compare=False)
     points: np.ndarray = field(compare=False, repr=False)
-    k: int = field(compare=False, default=1)
+    k: int = field(compare=False, default=1)          # kept for callers of the plain path; the stream inserts directly
     frac: float = field(compare=False, default=0.005)
 
 
@@ -40,144 +42,121 @@ class Result:
     start: float
     done: float
     simplices: np.ndarray | None
-    worker: int
-    batched: bool
+    status: int
+
+
+def calibrate(device: int = 0, dim: int = 3, small: int = 1 << 16, large: int = 1 << 18) -> tuple[float, float]:
+    """Device bytes of a stream as a + b * capacity, measured: two streams of
+    `small` and `large` points are opened on `device` and their reported
+    device bytes are fitted.  Returns (a, b)."""
+    out = []
+    for cap in (small, large):
+        with Triangulator(device) as tri:
+            st = Stream(tri, dim, cap, 64)
+            out.append(st.info()["device_bytes"])
+            st.close()
+    b = (out[1] - out[0]) / (large - small)
+    return out[0] - b * small, b
 
 
 class Server:
-    """Admission, batching and execution of jobs on `workers` contexts.
+    """One stream on `device`; capacity = (budget_bytes - fixed) / per point,
+    from `calibrate` (or the model given), at most 2^25 points."""
 
-    bytes_per_point: device-memory model of one job (measured once from the
-    library's pool after a run of the target shape; see calibrate()).
-    """
-
-    def __init__(self, device: int = 0, workers: int = 3, budget_bytes: float = 120e9,
-                 bytes_per_point: float = 6000.0, small_job: int = 65_536, batch_points: int = 2_000_000,
-                 keep_results: bool = True, **config):
+    def __init__(self, device: int = 0, dim: int = 3, budget_bytes: float = 120e9, max_jobs: int = 256,
+                 model: tuple[float, float] | None = None, keep_results: bool = True, capacity: int | None = None,
+                 **config):
         self.device = device
-        self.workers = workers
+        self.dim = dim
         self.budget = float(budget_bytes)
-        self.bpp = float(bytes_per_point)
-        self.small_job = small_job
-        self.batch_points = batch_points
+        self.model = model or calibrate(device, dim)
+        fixed, per_point = self.model
+        cap = int((self.budget - fixed) / per_point) if capacity is None else int(capacity)
+        self.capacity = max(1 << 12, min(cap, (1 << 25)))
+        self.max_jobs = max_jobs
         self.keep = keep_results
         self.config = config
-        self._lock = threading.Condition()
-        self._queue: list[Job] = []            # arrived, not yet admitted (by arrival time)
-        self._reserved = 0.0
         self._results: list[Result] = []
-        self._rows_out = 0                      # simplices copied back to the host
-        self._launches = 0                      # CUDA kernels launched by the library
-        self._closed = False
+        self._rows_out = 0
+        self._launches = 0
+        self._lock = threading.Condition()
         self._t0 = None
-        self.peak_reserved = 0.0
-
-    # ------------------------------------------------------------------ model
-    def estimate(self, n: int) -> float:
-        return self.bpp * n + 64e6
-
-    # ------------------------------------------------------------------ clients
-    def submit(self, job: Job):
-        with self._lock:
-            heapq.heappush(self._queue, job)
-            self._lock.notify_all()
-
-    def close(self):
-        with self._lock:
-            self._closed = True
-            self._lock.notify_all()
+        self.peak_running_points = 0
+        self.info = {}
 
     def now(self) -> float:
         return time.perf_counter() - self._t0
 
-    # ------------------------------------------------------------------ scheduling
-    def _take(self):
-        """Next work unit for a free worker: one large job, or a pack of the
-        small jobs waiting now, limited by the memory budget.  None = wait."""
-        if not self._queue:
-            return None
-        head = self._queue[0]
-        n = len(head.points)
-        if n > self.small_job:
-            need = self.estimate(n)
-            if self._reserved + need > self.budget and self._reserved > 0:
-                return None
-            heapq.heappop(self._queue)
-            self._reserved += need
-            return [head], need
-        pack, total, need = [], 0, 0.0
-        rest = []
-        while self._queue:
-            j = heapq.heappop(self._queue)
-            m = len(j.points)
-            e = self.estimate(m)
-            if m <= self.small_job and total + m <= self.batch_points and \
-                    (self._reserved + need + e <= self.budget or not pack and self._reserved == 0):
-                pack.append(j)
-                total += m
-                need += e
-            else:
-                rest.append(j)
-        for j in rest:
-            heapq.heappush(self._queue, j)
-        if not pack:
-            return None
-        self._reserved += need
-        return pack, need
-
-    def _worker(self, w: int):
+    def run(self, jobs: list[Job], realtime: bool = True) -> dict:
+        """Replays `jobs` (arrival times in seconds from the start): a feeder
+        thread submits each job at its arrival time while this thread drives
+        the engine and collects finished jobs."""
         tri = Triangulator(self.device, **self.config)
+        stream = Stream(tri, self.dim, self.capacity, self.max_jobs)
+        ids = {}                              # library job id -> Job
+        start = {}
+        submitted = [0]
+        errors = []
+        self._t0 = time.perf_counter()
+        order = sorted(jobs, key=lambda j: j.arrival)
+
+        def feeder():
+            try:
+                for j in order:
+                    if realtime:
+                        delay = j.arrival - self.now()
+                        if delay > 0:
+                            time.sleep(delay)
+                    jid = stream.submit(j.points)
+                    with self._lock:
+                        ids[jid] = j
+                        start[jid] = self.now()
+                        submitted[0] += 1
+                        self._lock.notify_all()
+            except Exception as e:            # reported by the driver loop
+                errors.append(e)
+                with self._lock:
+                    submitted[0] = len(order)
+                    self._lock.notify_all()
+
+        th = threading.Thread(target=feeder, daemon=True)
+        th.start()
+        finished: set[int] = set()
+        l0 = stream.info()["launches"]
         try:
             while True:
                 with self._lock:
-                    while True:
-                        unit = self._take()
-                        if unit is not None:
+                    open_ids = [jid for jid in ids if jid not in finished]
+                    all_in = submitted[0] == len(order)
+                    if not open_ids:
+                        if all_in:
                             break
-                        if self._closed and not self._queue:
-                            return
-                        self._lock.wait(timeout=0.005)
-                    self.peak_reserved = max(self.peak_reserved, self._reserved)
-                jobs, need = unit
-                start = self.now()
-                if len(jobs) == 1 and len(jobs[0].points) > self.small_job:
-                    j = jobs[0]
-                    out = tri.triangulate(j.points, k=j.k, sample_frac=j.frac, fetch=True)
-                    outs, batched = [out], False
-                else:
-                    P = np.concatenate([j.points for j in jobs]) if len(jobs) > 1 else jobs[0].points
-                    off = np.zeros(len(jobs) + 1, dtype=np.int64)
-                    off[1:] = np.cumsum([len(j.points) for j in jobs])
-                    outs, batched = tri.triangulate_batch(P, off), True
-                done = self.now()
-                launched = tri.stats().launches
-                with self._lock:
-                    self._reserved -= need
-                    self._rows_out += sum(len(o) for o in outs)
-                    self._launches += launched
-                    for j, o in zip(jobs, outs):
-                        self._results.append(Result(j.jid, len(j.points), j.arrival, start, done,
-                                                    o if self.keep else None, w, batched))
-                    self._lock.notify_all()
+                        self._lock.wait(timeout=0.01)      # nothing in flight: wait for an arrival
+                        continue
+                stream.run(1)                              # admit, then rounds until a job ends or one arrives
+                info = stream.info()
+                self.peak_running_points = max(self.peak_running_points, info["capacity"] - info["free_points"])
+                for jid in open_ids:
+                    st, _ = stream.status(jid)
+                    if st in (0, 1):
+                        continue
+                    rows = stream.fetch(jid) if st == 2 else None
+                    t = self.now()
+                    j = ids[jid]
+                    self._results.append(Result(j.jid, len(j.points), j.arrival, start[jid], t,
+                                                rows if self.keep else None, st))
+                    if rows is not None:
+                        self._rows_out += len(rows)
+                    stream.release(jid)
+                    finished.add(jid)
+            if errors:
+                raise errors[0]
         finally:
+            th.join(timeout=60)
+            self.info = stream.info()
+            self._launches = self.info["launches"] - l0
+            stream.close()
             tri.close()
-
-    # ------------------------------------------------------------------ driver
-    def run(self, jobs: list[Job], realtime: bool = True) -> dict:
-        """Replays `jobs` (arrival times in seconds from start) and serves them."""
-        self._t0 = time.perf_counter()
-        threads = [threading.Thread(target=self._worker, args=(w,), daemon=True) for w in range(self.workers)]
-        for t in threads:
-            t.start()
-        for j in sorted(jobs, key=lambda j: j.arrival):
-            if realtime:
-                delay = j.arrival - self.now()
-                if delay > 0:
-                    time.sleep(delay)
-            self.submit(j)
-        self.close()
-        for t in threads:
-            t.join()
         return self.summary()
 
     def results(self) -> list[Result]:
@@ -193,9 +172,11 @@ class Server:
         return {"jobs": len(res), "points": pts, "makespan_s": span,
                 "throughput_mpts": pts / span / 1e6 if span > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3), "batched_jobs": sum(r.batched for r in res),
-                "peak_reserved_gb": self.peak_reserved / 1e9, "rows_out": self._rows_out,
-                "launches": self._launches}
+                "mean_ms": float(lat.mean() * 1e3), "failed": sum(r.status != 2 for r in res),
+                "capacity_points": self.capacity, "peak_running_points": self.peak_running_points,
+                "device_gb": self.info.get("device_bytes", 0) / 1e9, "quanta": self.info.get("quanta", 0),
+                "rounds": self.info.get("rounds", 0), "rows_out": self._rows_out, "launches": self._launches,
+                "model_bytes_per_point": self.model[1]}
 
 
 def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
@@ -204,11 +185,12 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
 
 
 def k_for(n: int, divide: bool = False) -> int:
-    """Partitions for a job of n points.  On one GPU the direct insertion
-    (k = 1) was faster than the divide-and-conquer path at every size measured
-    (1k to 4M points: the border triangulation and the sample DT cost more
-    than the smaller partial triangulations save), so jobs run directly unless
-    `divide` asks for about 64k points per partition."""
+    """Partitions for a job of n points on the plain path.  On one GPU the
+    direct insertion (k = 1) was faster than the divide-and-conquer path at
+    every size measured (1k to 4M points: the border triangulation and the
+    sample DT cost more than the smaller partial triangulations save), so
+    jobs run directly unless `divide` asks for about 64k points per
+    partition."""
     if not divide or n < 131_072:
         return 1
     return int(min(64, max(2, 2 ** round(math.log2(n / 65_536)))))

@@ -1,8 +1,7 @@
-"""Serving: jobs arriving over time are admitted by a device-memory budget,
-small ones batched together, large ones divided, on several concurrent
-workers (contexts and streams).  Each job's result in the mix must equal its
-result alone: the oracle's DT for small jobs, a standalone library run for
-the large ones (integer output: bit-exact)."""
+"""Serving: Poisson arrivals of 3D jobs of mixed sizes, admitted by a
+device-memory budget into one resident engine that batches them round by
+round (continuous batching).  Each job's result in the mix must equal its
+result alone: the oracle's DT of its points (integer output: bit-exact)."""
 import numpy as np
 import pytest
 
@@ -13,43 +12,37 @@ pytestmark = pytest.mark.gpu
 
 
 def _jobs(count, seed, lo, hi, rate):
-    from paper_1902_07554_gb300.serve import Job, k_for, poisson_arrivals
+    from paper_1902_07554_gb300.serve import Job, poisson_arrivals
     sizes, kinds, seeds = pointsets.serve_jobs(count, seed=seed, lo=lo, hi=hi)
     arr = poisson_arrivals(count, rate, seed)
-    jobs = []
-    for i in range(count):
-        P = pointsets.job_points(sizes[i], kinds[i], seeds[i])
-        jobs.append(Job(float(arr[i]), i, P, k=k_for(len(P), divide=True), frac=0.005))
-    return jobs
+    return [Job(float(arr[i]), i, pointsets.job_points(sizes[i], kinds[i], seeds[i])) for i in range(count)]
 
 
 def test_results_in_the_mix_equal_results_alone():
-    from paper_1902_07554_gb300 import Triangulator
     from paper_1902_07554_gb300.serve import Server
     jobs = _jobs(24, 11, 1000, 300_000, rate=40.0)
-    srv = Server(workers=3, budget_bytes=6e9, bytes_per_point=4000.0, small_job=20_000, batch_points=200_000)
+    srv = Server(budget_bytes=6e9)
     summary = srv.run(jobs)
-    assert summary["jobs"] == 24
-    assert summary["batched_jobs"] > 0 and summary["p99_ms"] >= summary["p50_ms"] > 0
+    assert summary["jobs"] == 24 and summary["failed"] == 0
+    assert summary["p99_ms"] >= summary["p50_ms"] > 0 and summary["quanta"] > 1
     res = {r.jid: r for r in srv.results()}
-    with Triangulator(0) as alone:
-        for j in jobs:
-            got = res[j.jid].simplices.astype(np.int64)
-            if len(j.points) <= 20_000:
-                want = oracle.delaunay(j.points)
-            else:
-                want = alone.triangulate(j.points, k=j.k, sample_frac=j.frac).astype(np.int64)
-            assert np.array_equal(got, want), j.jid
+    for j in jobs:
+        assert np.array_equal(res[j.jid].simplices.astype(np.int64), oracle.delaunay(j.points)), j.jid
 
 
 def test_admission_respects_the_budget():
-    from paper_1902_07554_gb300.serve import Server
+    """The stream is sized from the budget with the measured per-point cost,
+    and the points in flight never exceed it."""
+    from paper_1902_07554_gb300.serve import Server, calibrate
+    fixed, per_point = calibrate(0, 3)
+    assert per_point > 0 and fixed > 0
+    budget = fixed + per_point * 80_000
     jobs = _jobs(16, 3, 1000, 40_000, rate=1000.0)        # everything arrives at once
-    budget = 4000.0 * 60_000 + 64e6                         # room for about one large job at a time
-    srv = Server(workers=4, budget_bytes=budget, bytes_per_point=4000.0, small_job=10_000,
-                 batch_points=60_000, keep_results=False)
-    srv.run(jobs)
-    assert srv.peak_reserved <= budget
+    srv = Server(budget_bytes=budget, model=(fixed, per_point), keep_results=False)
+    assert srv.capacity == 80_000
+    s = srv.run(jobs)
+    assert s["failed"] == 0 and s["peak_running_points"] <= srv.capacity
+    assert s["device_gb"] * 1e9 <= budget * 1.01
 
 
 def test_large_job_in_the_mix_matches_oracle():
@@ -61,9 +54,9 @@ def test_large_job_in_the_mix_matches_oracle():
     sizes, kinds, seeds = pointsets.serve_jobs(10, seed=21, lo=1000, hi=100_000)
     for i in range(10):
         jobs.append(Job(0.01 * (i + 1), i + 1, pointsets.job_points(sizes[i], kinds[i], seeds[i])))
-    srv = Server(workers=3)
+    srv = Server(budget_bytes=12e9)
     summary = srv.run(jobs)
-    assert summary["jobs"] == 11
+    assert summary["jobs"] == 11 and summary["failed"] == 0
     res = {r.jid: r for r in srv.results()}
     assert np.array_equal(res[0].simplices.astype(np.int64), oracle.delaunay(big))
     for j in jobs[1:]:

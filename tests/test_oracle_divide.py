@@ -309,7 +309,7 @@ def test_multilevel_hand_derived_case():
     PS = np.stack([np.arange(n, dtype=np.float64), np.zeros(n)], axis=1)
     assert dv.partition(PS, E, w, k, eps, rounds=2).tolist() == [int(x) for x in g["ml.lp2"]]
     tr = {}
-    got = dv.ml_partition(PS, E, w, k, eps, rounds=2, trace=tr)
+    got = dv.ml_partition(PS, E, w, k, eps, rounds=2, trace=tr, coarse_rounds=2)
     assert tr["sizes"] == [8, 4]
     assert tr["mates"][0].tolist() == [int(x) for x in g["ml.mate"]]
     assert tr["cmaps"][0].tolist() == [int(x) for x in g["ml.cmap"]]
