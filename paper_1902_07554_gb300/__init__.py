@@ -53,7 +53,8 @@ class Config(ctypes.Structure):
                 ("small_rounds", ctypes.c_int), ("brio_drain", ctypes.c_int),
                 ("partition_init", ctypes.c_int), ("recursive", ctypes.c_int),
                 ("active_ratio", ctypes.c_int), ("nominate_rings", ctypes.c_int), ("partitioner", ctypes.c_int),
-                ("round_limit", ctypes.c_int), ("walk_limit", ctypes.c_int), ("arena_factor", ctypes.c_int)]
+                ("round_limit", ctypes.c_int), ("walk_limit", ctypes.c_int), ("arena_factor", ctypes.c_int),
+                ("cavity_blocks", ctypes.c_int)]
 
 
 class KernelProfile(ctypes.Structure):

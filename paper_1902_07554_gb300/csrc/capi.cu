@@ -44,7 +44,7 @@ static bool cfg_valid(const dt_config* c) {
          (c->recursive == 0 || c->recursive == 1) && c->active_ratio >= 0 && c->active_ratio <= 10000 &&
          c->nominate_rings >= 0 && c->nominate_rings <= 2 && (c->partitioner == DT_PART_LP ||
          c->partitioner == DT_PART_MULTILEVEL) && c->round_limit >= 0 && c->walk_limit >= 0 &&
-         c->arena_factor >= 0 && c->arena_factor <= 1024;
+         c->arena_factor >= 0 && c->arena_factor <= 1024 && c->cavity_blocks >= 0 && c->cavity_blocks <= 64;
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {
@@ -66,6 +66,11 @@ extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_c
     c->own_stream = true;
   }
   if (cfg) c->cfg = *cfg; else dt_config_default(&c->cfg);
+  {
+    int m = 0;
+    if (cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && m > 0) c->sms = m;
+    else cudaGetLastError();
+  }
   if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&c->status_host, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&c->counters_host, 64 * sizeof(int)) != cudaSuccess) {

@@ -11,6 +11,7 @@ namespace gdt { class JobQueue; struct StreamState; }
 
 struct dt_ctx {
   int device = 0;
+  int sms = 152;                         // streaming multiprocessors of the device (grid sizes)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;     // capture stream of the insertion-round graph
   bool pdl_ok = true;                    // programmatic launches accepted in the round graph

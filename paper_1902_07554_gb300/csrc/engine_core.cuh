@@ -1306,10 +1306,11 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
   const int capCand = (int)std::max<int64_t>(1, std::min<int64_t>(npts, int64_t(1) << 22));
   int64_t max_level = 1;
   for (size_t l = 0; l + 1 < loff.size(); l++) max_level = std::max<int64_t>(max_level, loff[l + 1] - loff[l]);
-  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div<int64_t>(npts, 256), 152 * 8);
-  const unsigned gr = (unsigned)std::min<int64_t>(ceil_div<int64_t>(npts, 128), 152 * 16);
-  const unsigned ga = (unsigned)std::min<int64_t>(ceil_div<int64_t>(max_level, 128), 152 * 16);
-  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
+  const int64_t sms = c->sms, cb = c->cfg.cavity_blocks > 0 ? c->cfg.cavity_blocks : 16;
+  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div<int64_t>(npts, 256), sms * 8);
+  const unsigned gr = (unsigned)std::min<int64_t>(ceil_div<int64_t>(npts, 128), sms * 16);
+  const unsigned ga = (unsigned)std::min<int64_t>(ceil_div<int64_t>(max_level, 128), sms * 16);
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), sms * cb);
   EngCtl h1;
   memset(&h1, 0, sizeof(h1));
   for (int grow = 0;; grow++) {
@@ -1725,7 +1726,8 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       CUDA_OK(cudaMemsetAsync(cnt + 1, 0, 20, s));
       CUDA_OK(cudaMemsetAsync(cnt + 8, 0, 4 * NBUCKET, s));
       unsigned gp = (unsigned)ceil_div(nact, 256);
-      unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
+      unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128),
+                                                (int64_t)c->sms * (c->cfg.cavity_blocks > 0 ? c->cfg.cavity_blocks : 16));
       int ev[6];
       ev[0] = mark();
       k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2, cnt + 8, capCand,
@@ -2259,9 +2261,10 @@ static int stream_graph(dt_ctx* c, StreamState& st, cudaGraphConditionalHandle* 
   TriView<D> T = stream_view<D>(c, st);
   const int capCand = (int)st.cap_cand;
   const int J = st.max_jobs;
-  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div<int64_t>(st.cap, 256), 152 * 8);
-  const unsigned gr = (unsigned)std::min<int64_t>(ceil_div<int64_t>(st.cap, 128), 152 * 16);
-  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), 152 * 16);
+  const int64_t sms = c->sms, cb = c->cfg.cavity_blocks > 0 ? c->cfg.cavity_blocks : 16;
+  const unsigned gn = (unsigned)std::min<int64_t>(ceil_div<int64_t>(st.cap, 256), sms * 8);
+  const unsigned gr = (unsigned)std::min<int64_t>(ceil_div<int64_t>(st.cap, 128), sms * 16);
+  const unsigned gw = (unsigned)std::min<int64_t>(ceil_div<int64_t>((int64_t)capCand * 32, 128), sms * cb);
   const int drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
   const unsigned tb = (unsigned)std::min(1024, std::max(32, ((J + 31) / 32) * 32));
   cudaGraph_t g = nullptr;
@@ -2336,10 +2339,14 @@ template <int D>
 static int stream_quantum_t(dt_ctx* c, StreamState& st, int* yield) {
   cudaStream_t s = c->stream;
   for (int grow = 0;; grow++) {
+    // the graph bakes configuration values in (walk limit, rings, tiles): rebuild it
+    // when the context's configuration changed since it was built
+    if (st.gx && memcmp(&st.graph_cfg, &c->cfg, sizeof(dt_config)) != 0) stream_release_graph(st);
     if (!st.gx) {
       cudaGraphConditionalHandle hc;
       int rc = stream_graph<D>(c, st, &hc);
       if (rc) return rc;
+      st.graph_cfg = c->cfg;
     }
     const int drain = c->cfg.brio_drain > 1 ? c->cfg.brio_drain : 8;
     const unsigned tb = (unsigned)std::min(1024, std::max(32, ((st.max_jobs + 31) / 32) * 32));

@@ -71,6 +71,7 @@ struct StreamState {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t gx = nullptr;
   bool graph_pdl = true;
+  dt_config graph_cfg;           // the context's configuration the graph was built with
   unsigned round = 0;
   long long quanta = 0, rounds_run = 0;
   // host bookkeeping (mu guards queue, jobs and next_id: dt_stream_submit may

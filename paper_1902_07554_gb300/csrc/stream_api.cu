@@ -70,6 +70,7 @@ int stream_fail_running(dt_ctx* c, int code) {
     st.free_ranges.assign(1, {0, st.cap});
   }
   cudaGetLastError();
+  stream_release_graph(st);
   return st.dim == 2 ? stream_setup_2d(c, st) : stream_setup_3d(c, st);
 }
 

@@ -1,8 +1,11 @@
 """Schedule autotuning of the insertion engine for a workload shape.
 
-The engine's round schedule has three knobs in dt_config: brio_growth (batch
-growth x 100), brio_drain (how far the active set drains before the next
-batch) and first_batch (points per instance in the first batch).  The best
+The engine's schedule has five knobs in dt_config: brio_growth (batch growth
+x 100), brio_drain (how far the active set drains before the next batch),
+first_batch (points per instance in the first batch), nominate_rings (the
+neighbour rings in which a nominee must hold the strongest pick: the queue of
+regions grown per round) and cavity_blocks (the tile of the region-growth and
+insertion kernels: thread blocks per SM).  The best
 setting depends on the shape of the work -- one large instance, a few
 partitions, or thousands of small batched instances -- so `autotune` times a
 small grid of candidates on a representative input through the library's
@@ -18,7 +21,11 @@ import time
 
 import numpy as np
 
-DEFAULT_GRID = {"brio_growth": (125, 150, 200), "brio_drain": (4, 8), "first_batch": (32, 128)}
+# round schedule (BRIO growth, drain, first batch), nominee queue policy (the
+# rings a nominee must hold the strongest pick in) and the cavity tiles (thread
+# blocks per SM of the region-growth and insertion kernels)
+DEFAULT_GRID = {"brio_growth": (125, 150, 200), "brio_drain": (4, 8), "first_batch": (32, 128),
+                "nominate_rings": (1, 2), "cavity_blocks": (8, 16)}
 
 _cache: dict = {}
 

@@ -110,3 +110,20 @@ def test_batch2d_4096_full_size_every_instance(tri):
     for i in bad[:3]:
         assert np.array_equal(res[i].astype(np.int64), oracle.delaunay(P[off[i]:off[i + 1]])), i
     assert not bad, bad[:20]
+
+
+def test_autotuned_schedule_keeps_parity(tri):
+    """The autotuner times every candidate schedule (round schedule, nominee
+    queue, cavity tiles) on a batch and applies the fastest; the batch
+    triangulated under it equals the oracle instance by instance."""
+    from paper_1902_07554_gb300 import tune
+    P, off = _mixed(80, 17, 200, 6000)
+    tune.clear_cache()
+    r = tune.autotune(tri, P, offsets=off, reps=1, use_cache=False)
+    assert len(r["table"]) == len(tune.candidates()) and set(r["best"]) == set(tune.DEFAULT_GRID)
+    res = tri.triangulate_batch(P, off)
+    try:
+        for i in range(len(off) - 1):
+            assert np.array_equal(res[i].astype(np.int64), oracle.delaunay(P[off[i]:off[i + 1]])), i
+    finally:
+        tri.configure(**{k: 0 for k in tune.DEFAULT_GRID})

@@ -39,19 +39,19 @@ class FakeTri:
 def test_picks_and_applies_the_fastest_schedule():
     tune.clear_cache()
     clk = FakeClock()
-    best = {"brio_growth": 200, "brio_drain": 4, "first_batch": 128}
+    best = {"brio_growth": 200, "brio_drain": 4, "cavity_blocks": 8, "first_batch": 128, "nominate_rings": 2}
     tri = FakeTri(clk, best)
     P = np.zeros((1000, 3))
     r = tune.autotune(tri, P, k=1, clock=clk)
     assert r["best"] == best and not r["cached"]
     assert tri.cfg == best
-    assert len(r["table"]) == len(tune.candidates()) == 12
-    assert len(tri.calls) == 12 * 3                      # one untimed + two timed runs each
+    assert len(r["table"]) == len(tune.candidates()) == 48   # 3 x 2 x 2 x 2 x 2
+    assert len(tri.calls) == 48 * 3                      # one untimed + two timed runs each
     assert abs(r["ms"] - 10.0) < 1e-9
     # the same shape again: applied from the cache, nothing timed
     tri.cfg = {}
     r2 = tune.autotune(tri, np.ones((1000, 3)), k=1, clock=clk)
-    assert r2["cached"] and tri.cfg == best and len(tri.calls) == 36
+    assert r2["cached"] and tri.cfg == best and len(tri.calls) == 48 * 3
 
 
 def test_batch_shapes_and_ties():
