@@ -114,6 +114,8 @@ extern "C" void dt_destroy(dt_ctx* c) {
   }
   c->round_graphs.clear();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  for (cudaEvent_t e : c->aux_ev) if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

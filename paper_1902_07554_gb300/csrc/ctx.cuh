@@ -14,6 +14,8 @@ struct dt_ctx {
   int sms = 152;                         // streaming multiprocessors of the device (grid sizes)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;     // capture stream of the insertion-round graph
+  cudaStream_t aux_stream = nullptr;     // second stream: the label walk beside the partitioner
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
   bool pdl_ok = true;                    // programmatic launches accepted in the round graph
   // instantiated round graphs, keyed by the bytes of every launch parameter
   // captured in them: a run whose buffers, sizes and grids equal an earlier

@@ -536,8 +536,21 @@ __global__ void k_label_walk(const typename PT<D>::T* P, int64_t n, const typena
     v = nv;
     if (step == m) set_error(st, DT_E_TIMEOUT, 20);
   }
-  label[i] = block[v];
+  if (label) label[i] = block[v];
   if (nearest) nearest[i] = v;
+}
+
+// label[i] = block[nearest[i]]: the labels once the partition is known (the walk to the
+// nearest sample point does not depend on the blocks and can run beside the partitioner).
+__global__ void k_map_labels(const int* nearest, const int* block, int64_t n, int* label) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) label[i] = block[nearest[i]];
+}
+
+int map_labels(dt_ctx* c, const int* nearest, const int* block, int64_t n, int* label) {
+  if (n > 0)
+    k_map_labels<<<(unsigned)ceil_div<int64_t>(n, 256), 256, (++c->launches, 0), c->stream>>>(nearest, block, n, label);
+  return 0;
 }
 
 int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, const int* srank, const SampleGraph& G,

@@ -31,6 +31,7 @@ int partition_multilevel(dt_ctx* c, const SampleGraph& G, int k, double eps, int
 int cut_weight(dt_ctx* c, const SampleGraph& G, const int* block, long long* out);
 int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, const int* srank, const SampleGraph& G,
                  const int* block, int* label, int* nearest);
+int map_labels(dt_ctx* c, const int* nearest, const int* block, int64_t n, int* label);
 int kd_divide(dt_ctx* c, int dim, const void* P, int64_t n, int k, int* label, const char* tag = "kd");
 int scatter_by_label(dt_ctx* c, int dim, const void* P, const int* label, int64_t n, int k, void* Ps, int* gid,
                      int* pinst, std::vector<int64_t>& poff, std::vector<int64_t>& sizes_out);

@@ -123,14 +123,36 @@ static int run_dc(dt_ctx* c, const void* P, int64_t n, int dim, int k, double fr
     rc = sample_graph(c, c->run_sample, PS, dim, cfg.weight, G);
     if (rc) return rc;
     cudaEventRecord(c->ev[3], s);
+    // Alg. 2's assignment walk needs the sample DT but not the blocks: it runs on a
+    // second stream beside the partitioner, and the labels are mapped once both are done
+    int* nearest = (int*)pool_get(c, "dc.nearest", 4 * (size_t)n);
+    if (!nearest) return set_err(c, DT_E_NOMEM, "nearest sample points");
+    if (!c->aux_stream && cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->aux_stream = nullptr;
+    }
+    for (cudaEvent_t& e : c->aux_ev)
+      if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { cudaGetLastError(); e = nullptr; }
+    const bool aux = c->aux_stream && c->aux_ev[0] && c->aux_ev[1];
+    if (aux) {
+      CUDA_OK(cudaEventRecord(c->aux_ev[0], s));
+      CUDA_OK(cudaStreamWaitEvent(c->aux_stream, c->aux_ev[0], 0));
+      c->stream = c->aux_stream;
+    }
+    rc = label_points(c, dim, P, n, PS, ids, G, nullptr, nullptr, nearest);
+    if (aux) {
+      cudaEventRecord(c->aux_ev[1], c->aux_stream);
+      c->stream = s;
+    }
+    if (rc) return rc;
     rc = partition_graph(c, PS, dim, G, k, cfg.epsilon, cfg.lp_rounds, cfg.partition_init, block);
     if (rc) return rc;
     long long cut = 0;
     rc = cut_weight(c, G, block, &cut);
     if (rc) return rc;
     c->stats.cut_weight = cut;
-    rc = label_points(c, dim, P, n, PS, ids, G, block, c->labels, nullptr);
-    if (rc) return rc;
+    if (aux) CUDA_OK(cudaStreamWaitEvent(s, c->aux_ev[1], 0));
+    map_labels(c, nearest, block, n, c->labels);
     c->sample = ids;
     c->sample_block = block;
     c->eta = eta;
