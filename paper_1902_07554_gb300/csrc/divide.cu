@@ -513,23 +513,68 @@ __global__ void k_dilate(const int* in, int* out, StartGrid sg, int64_t ncell) {
   out[id] = v;
 }
 
+// FP32 copies of the sample points relative to the origin o (the centre of the
+// points' bounding box): X = fl32(fl64(x - o)).
+template <int D>
+__global__ void k_sample_x32(const typename PT<D>::T* S, int64_t m, StartGrid sg, double3 o, float4* XS) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const typename PT<D>::T q = S[j];
+  XS[j] = make_float4((float)(cx(q) - o.x), (float)(cy(q) - o.y), D == 3 ? (float)(cz(q) - o.z) : 0.0f, 0.0f);
+}
+
+// First stage of sign(|p - a|^2 - |p - b|^2) in FP32 with a rigorous bound.
+// Every copy X = fl32(fl64(x - o)) is within (u32 + 2 u64) R of x - o (R: the
+// largest |x_c - o_c|), so a difference A = fl32(Xa - Xp) is within
+// e(A) = eta + u32 |A| (1 + 2 u32) of a - p, eta = 2 (u32 + 2 u64) R.  Then
+// |A^2 - (a - p)^2| <= e (2 |A| + e), the sums of three squares are exact to
+// gamma_3 = 3 u32 / (1 - 3 u32) of themselves and the final difference to u32
+// of itself; the bound is evaluated in FP32 and enlarged by 0.1 % to cover its
+// own roundings.  Returns -1 / +1 when decided, 0 when the FP64 test must run.
+template <int D>
+__device__ __forceinline__ int closer_f32(const float4& xp, const float4& xa, const float4& xb, float eta) {
+  const float u = 5.9604645e-8f;                      // 2^-24
+  const float ax = xa.x - xp.x, ay = xa.y - xp.y, az = D == 3 ? xa.z - xp.z : 0.0f;
+  const float bx = xb.x - xp.x, by = xb.y - xp.y, bz = D == 3 ? xb.z - xp.z : 0.0f;
+  const float sa = fmaf(az, az, fmaf(ay, ay, ax * ax));
+  const float sb = fmaf(bz, bz, fmaf(by, by, bx * bx));
+  const float d = sa - sb;
+  auto term = [&](float t) {
+    const float at = fabsf(t), e = fmaf(u * (1.0f + 2.0f * u), at, eta);
+    return e * (2.0f * at + e);
+  };
+  const float g3 = 3.0f * u / (1.0f - 3.0f * u);
+  const float err = 1.001f * (g3 * (1.0f + g3) * (sa + sb) + term(ax) + term(ay) + term(az) + term(bx) + term(by) +
+                              term(bz)) + 2.0f * u * fabsf(d);
+  if (!(err < 1e30f) || !(sa + sb > 1e-30f)) return 0;   // outside the range the bound covers
+  if (d > err) return 1;
+  if (d < -err) return -1;
+  return 0;
+}
+
 // Greedy walk on the sample Delaunay graph to the exactly nearest sample
-// point (ties: smaller global index); label = its block.
+// point (ties: smaller global index); label = its block.  Distances are
+// compared in FP32 first (closer_f32), in FP64 and exactly (closer) when that
+// cannot decide.
 template <int D>
 __global__ void k_label_walk(const typename PT<D>::T* P, int64_t n, const typename PT<D>::T* S, const int* srank,
                              const int* rowptr, const int* col, const int* block, const int* cellv, StartGrid sg,
-                             int64_t m, int* label, int* nearest, DevStatus* st) {
+                             int64_t m, int* label, int* nearest, DevStatus* st, const float4* XS, double3 o,
+                             float eta) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   typename PT<D>::T p = P[i];
+  const float4 xp = make_float4((float)(cx(p) - o.x), (float)(cy(p) - o.y), D == 3 ? (float)(cz(p) - o.z) : 0.0f, 0.0f);
   int v = cellv[grid_cell<D>(p, sg)];
   if (v < 0 || v >= m) v = 0;
   for (int64_t step = 0; step <= m; step++) {
     int a = rowptr[v], b = rowptr[v + 1];
     int nv = -1;
+    const float4 xv = XS[v];
     for (int j = a; j < b; j++) {
       int w = col[j];
-      int cmp = closer(p, S[w], S[v], D);
+      int cmp = closer_f32<D>(xp, XS[w], xv, eta);
+      if (cmp == 0) cmp = closer(p, S[w], S[v], D);
       if (cmp < 0 || (cmp == 0 && srank[w] < srank[v])) { nv = w; break; }
     }
     if (nv < 0) break;
@@ -596,13 +641,27 @@ int label_points(dt_ctx* c, int dim, const void* P, int64_t n, const void* S, co
     else k_dilate<3><<<gc, 256, (++c->launches, 0), s>>>(cv0, cv1, sg, ncell);
     std::swap(cv0, cv1);
   }
+  // FP32 stage: origin at the box centre, eta = 2 (u32 + 2 u64) R rounded up
+  double oc[3] = {0, 0, 0}, R = 0.0;
+  for (int cc = 0; cc < dim; cc++) {
+    oc[cc] = 0.5 * hb[cc] + 0.5 * hb[3 + cc];
+    R = std::max(R, std::max(hb[3 + cc] - oc[cc], oc[cc] - hb[cc]));
+  }
+  const double3 o = make_double3(oc[0], oc[1], oc[2]);
+  const double etad = 2.02 * (std::ldexp(1.0, -24) + std::ldexp(1.0, -52)) * R * (1.0 + 1e-9);
+  float eta = (float)etad;
+  if (!((double)eta >= etad)) eta = std::nextafter(eta, INFINITY);
+  float4* XS = (float4*)pool_get(c, "lw.xs", 16 * (size_t)std::max<int64_t>(m, 1));
+  if (!XS) return set_err(c, DT_E_NOMEM, "label walk copies");
+  if (dim == 2) k_sample_x32<2><<<gm, 256, (++c->launches, 0), s>>>((const double2*)S, m, sg, o, XS);
+  else k_sample_x32<3><<<gm, 256, (++c->launches, 0), s>>>((const double4_32a*)S, m, sg, o, XS);
   unsigned gn = (unsigned)ceil_div<int64_t>(n, 128);
   if (dim == 2)
     k_label_walk<2><<<gn, 128, (++c->launches, 0), s>>>((const double2*)P, n, (const double2*)S, srank, G.rowptr, G.col, block, cv0, sg,
-                                       m, label, nearest, c->status);
+                                       m, label, nearest, c->status, XS, o, eta);
   else
     k_label_walk<3><<<gn, 128, (++c->launches, 0), s>>>((const double4_32a*)P, n, (const double4_32a*)S, srank, G.rowptr, G.col, block, cv0, sg,
-                                       m, label, nearest, c->status);
+                                       m, label, nearest, c->status, XS, o, eta);
   return 0;
 }
 

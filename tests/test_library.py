@@ -39,7 +39,8 @@ def test_config_default_and_bad_device():
 
 
 @pytest.mark.parametrize("cname,pyname", [("dt_config", "Config"), ("dt_stats", "Stats"),
-                                          ("dt_validation", "Validation"), ("dt_kernel_profile", "KernelProfile")])
+                                          ("dt_validation", "Validation"), ("dt_kernel_profile", "KernelProfile"),
+                                          ("dt_stream_info", "StreamInfo")])
 def test_binding_structs_match_the_header(tmp_path, cname, pyname):
     """The ctypes mirrors have the header's field names, offsets and size
     (compiled from include/dt.h with the host C compiler)."""
