@@ -133,6 +133,10 @@ typedef struct dt_config {
                             so a 3D run needs about 27); an arena that overflows is doubled and the run
                             repeated, three times at most, then the call fails with DT_E_OVERFLOW;
                             0 = automatic (36 in 3D, 8 in 2D) */
+  int cavity_blocks;     /* thread blocks per SM of the region-growth and insertion kernels (128 threads,
+                            one warp per nominee; the kernels loop over the nominees); 0 = automatic (16) */
+  int cavity_occupancy;  /* resident blocks per SM the region-growth kernel is compiled for: 8, 12 or 16
+                            (registers per thread capped at 64, 40, 32); 0 = automatic (8) */
 } dt_config;
 
 typedef struct dt_stats {

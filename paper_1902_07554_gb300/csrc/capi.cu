@@ -44,7 +44,9 @@ static bool cfg_valid(const dt_config* c) {
          (c->recursive == 0 || c->recursive == 1) && c->active_ratio >= 0 && c->active_ratio <= 10000 &&
          c->nominate_rings >= 0 && c->nominate_rings <= 2 && (c->partitioner == DT_PART_LP ||
          c->partitioner == DT_PART_MULTILEVEL) && c->round_limit >= 0 && c->walk_limit >= 0 &&
-         c->arena_factor >= 0 && c->arena_factor <= 1024 && c->cavity_blocks >= 0 && c->cavity_blocks <= 64;
+         c->arena_factor >= 0 && c->arena_factor <= 1024 && c->cavity_blocks >= 0 && c->cavity_blocks <= 64 &&
+         (c->cavity_occupancy == 0 || c->cavity_occupancy == 8 || c->cavity_occupancy == 12 ||
+          c->cavity_occupancy == 16);
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {

@@ -505,8 +505,8 @@ __device__ __forceinline__ void region_stats(const TriView<D>& T, bool has, int 
 // k_cavity_big (up to BIGCAP per round).
 constexpr int CAV_G = 32;
 
-template <int D>
-__global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
+template <int D, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
                                                   CandScratch S, const int* bcnt, const EngCtl* ctl) {
   pdl_enter();
   if (ctl) {
@@ -553,6 +553,16 @@ __global__ void __launch_bounds__(128, 8) k_cavity_w(TriView<D> T, const int* no
     }
     __syncwarp();
   }
+}
+
+// The region-growth kernel compiled for 8, 12 or 16 resident blocks per SM
+// (register caps 64, 40, 32 per thread): more resident warps hide more of the
+// load latency the growth waits on, fewer registers spill more.
+template <int D>
+static decltype(&k_cavity_w<D, 8>) cavity_kernel(int occupancy) {
+  if (occupancy >= 16) return &k_cavity_w<D, 16>;
+  if (occupancy >= 12) return &k_cavity_w<D, 12>;
+  return &k_cavity_w<D, 8>;
 }
 
 // Second growth of large region q (one warp).
@@ -1384,7 +1394,8 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
       cudaLaunchKernelEx(&l1, k_activate<D>, T, (const int*)llist, 0, (int*)nullptr, cnt + 0, 0u, (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, nom, cnt + 2, cnt + 8,
                          capCand, (const EngCtl*)ctl);
-      cudaLaunchKernelEx(&l3, k_cavity_w<D>, T, (const int*)nom, (const int*)(cnt + 2), 0u, S, (const int*)(cnt + 8),
+      cudaLaunchKernelEx(&l3, cavity_kernel<D>(c->cfg.cavity_occupancy), T, (const int*)nom, (const int*)(cnt + 2), 0u, S,
+                         (const int*)(cnt + 8),
                          (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l8, k_cavity_big<D>, T, 0u, S, (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l4, k_insert_w<D>, T, 0u, S, (const int*)(cnt + 2), cnt + 3, (const EngCtl*)ctl);
@@ -1733,7 +1744,8 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2, cnt + 8, capCand,
                                                         nullptr);
       ev[1] = mark();
-      k_cavity_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8, nullptr);
+      cavity_kernel<D>(c->cfg.cavity_occupancy)<<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8,
+                                                                                   nullptr);
       k_cavity_big<D><<<BIGCAP / 4, 128, (++c->launches, 0), s>>>(T, round, S, nullptr);
       ev[2] = mark();
       k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3, nullptr);
@@ -2303,7 +2315,8 @@ static int stream_graph(dt_ctx* c, StreamState& st, cudaGraphConditionalHandle* 
                        (const EngCtl*)ctl);
     cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, st.nom, cnt + 2, cnt + 8,
                        capCand, (const EngCtl*)ctl);
-    cudaLaunchKernelEx(&l3, k_cavity_w<D>, T, (const int*)st.nom, (const int*)(cnt + 2), 0u, st.S,
+    cudaLaunchKernelEx(&l3, cavity_kernel<D>(c->cfg.cavity_occupancy), T, (const int*)st.nom, (const int*)(cnt + 2), 0u,
+                       st.S,
                        (const int*)(cnt + 8), (const EngCtl*)ctl);
     cudaLaunchKernelEx(&l8, k_cavity_big<D>, T, 0u, st.S, (const EngCtl*)ctl);
     cudaLaunchKernelEx(&l4, k_insert_w<D>, T, 0u, st.S, (const int*)(cnt + 2), cnt + 3, (const EngCtl*)ctl);
