@@ -378,7 +378,8 @@ def run_batch(args, w):
     if args.autotune:                      # untimed: picks the schedule the timed steps use
         from paper_1902_07554_gb300 import tune
         r = tune.autotune(tri, P_dev, offsets=off, reps=1)
-        schedule = {"best": r["best"], "ms": r["ms"], "candidates": len(r["table"])}
+        schedule = {"best": r["best"], "ms": r["ms"], "candidates": len(r["table"]),
+                    "grid": {k: list(v) for k, v in tune.DEFAULT_GRID.items()}}
     for _ in range(args.warmup):
         tri.L.dt_triangulate_batch(tri.ctx, ctypes_ptr(P_dev), ctypes_ptr(off), len(off) - 1, 2)
     clk = ClockSampler(local)
@@ -412,7 +413,8 @@ def run_batch(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "instances": len(off) - 1, "points": n, "dim": 2,
                        "l2": "flushed before every step (256 MiB write)",
-                       "schedule": schedule or "default (brio_growth 150, brio_drain 8, first_batch 32)"},
+                       "schedule": schedule or "default (brio_growth 150, brio_drain 8, first_batch 32, "
+                                               "nominate_rings 1, cavity_blocks 16)"},
             "e2e": {"value": n / (sum(e2e) / len(e2e)) / 1e6, "unit": "Mpoints/s",
                     "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": nout * 12},
             "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu,

@@ -154,3 +154,18 @@ def test_single_block_rounds_match_oracle(tri, D, kind):
         finally:
             tri.configure(small_rounds=0)
         assert np.array_equal(got, want), sr
+
+
+@pytest.mark.parametrize("cfg", [dict(cavity_occupancy=12), dict(cavity_occupancy=16),
+                                 dict(nominate_rings=2, cavity_blocks=8), dict(active_ratio=25)])
+def test_schedule_knobs_match_oracle(tri, cfg):
+    """Launch shapes and schedules change which nominees win a round, never
+    the result: each gives the oracle's DT (plain path and 4 partitions)."""
+    P = pointsets.clustered(30_000, 21)
+    want = oracle.delaunay(P)
+    tri.configure(**cfg)
+    try:
+        for k in (1, 4):
+            assert np.array_equal(tri.triangulate(P, k=k, sample_frac=0.01).astype(np.int64), want), (cfg, k)
+    finally:
+        tri.configure(**{name: 0 for name in cfg})
