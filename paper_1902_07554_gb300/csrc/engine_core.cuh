@@ -404,11 +404,12 @@ __device__ __forceinline__ void grow_region(const TriView<D>& T, bool has, int p
     pbytes += sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1) + 16 + 4;
   }
   status = __shfl_sync(FULL, status, gbase);
-  int nc = 1, nbd = 0, h = 0;
+  int nc = 1, nbd = 0, h = 0, nsteps = 0;
   __syncwarp();
   for (;;) {
     const bool act = status == CAND_OK && h < nc;
     if (!__any_sync(FULL, act)) break;
+    nsteps += act;
     const int nc0 = nc;                                // region simplices known at this step
     int j = h + gl / (D + 1), i = gl % (D + 1);
     bool valid = act && gl < PER * (D + 1) && j < nc0;
@@ -476,6 +477,7 @@ __device__ __forceinline__ void grow_region(const TriView<D>& T, bool has, int p
     }
     __syncwarp();
   }
+  if (T.dbg && has && gl == 0) atomicAdd(&T.dbg[7], (unsigned long long)nsteps);   // [7] growth steps
   nc_out = nc;
   nbd_out = nbd;
   status_out = status;
@@ -500,12 +502,11 @@ __device__ __forceinline__ void region_stats(const TriView<D>& T, bool has, int 
   }
 }
 
-// Nominees in groups of CAV_G lanes (32 / CAV_G per warp), strongest list
-// first.  A region that outgrows the regular lists is queued for
-// k_cavity_big (up to BIGCAP per round).
-constexpr int CAV_G = 32;
-
-template <int D, int MINB>
+// Nominees in groups of G lanes (32 / G per warp), strongest list first.  A
+// region that outgrows the regular lists is queued for k_cavity_big (up to
+// BIGCAP per round).  G = 16 puts two nominees in one warp: four region
+// simplices per step each, twice the nominees in flight per warp.
+template <int D, int MINB, int G>
 __global__ void __launch_bounds__(128, MINB) k_cavity_w(TriView<D> T, const int* nom, const int* nnom_p, unsigned round,
                                                   CandScratch S, const int* bcnt, const EngCtl* ctl) {
   pdl_enter();
@@ -513,8 +514,8 @@ __global__ void __launch_bounds__(128, MINB) k_cavity_w(TriView<D> T, const int*
     if (ctl->small || ctl->done) return;
     round = ctl->round;
   }
-  constexpr int GPW = 32 / CAV_G;                      // groups per warp
-  const int lane = threadIdx.x & 31, grp = lane / CAV_G, gl = lane % CAV_G;
+  constexpr int GPW = 32 / G;                          // groups per warp
+  const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarp = (gridDim.x * blockDim.x) >> 5;
   const int nnom = min(*nnom_p, S.cap);
@@ -538,10 +539,10 @@ __global__ void __launch_bounds__(128, MINB) k_cavity_w(TriView<D> T, const int*
     if (has && gl == 0) S.cand[slot] = p;
     unsigned long long pbytes = 0, ptests = 0;
     int nc, nbd, status;
-    grow_region<D, CAV_G>(T, has, p, key, C, NB, B, S.capC, S.capB, nc, nbd, status, pbytes, ptests);
+    grow_region<D, G>(T, has, p, key, C, NB, B, S.capC, S.capB, nc, nbd, status, pbytes, ptests);
     if (has && in_shared && status == CAND_OK)
-      for (int q = gl; q < nc; q += CAV_G) Cg[q] = C[q];
-    region_stats<D, CAV_G>(T, has, status, nc, pbytes, ptests);
+      for (int q = gl; q < nc; q += G) Cg[q] = C[q];
+    region_stats<D, G>(T, has, status, nc, pbytes, ptests);
     if (has && gl == 0) {
       if (status == CAND_OVER) {
         if (T.dbg) atomicAdd(&T.dbg[6], 1ull);
@@ -557,18 +558,121 @@ __global__ void __launch_bounds__(128, MINB) k_cavity_w(TriView<D> T, const int*
 
 // The region-growth kernel compiled for 8, 12 or 16 resident blocks per SM
 // (register caps 64, 40, 32 per thread): more resident warps hide more of the
-// load latency the growth waits on, fewer registers spill more.
+// load latency the growth waits on, fewer registers spill more.  group = 16:
+// two nominees per warp (8 blocks per SM).
 template <int D>
-static decltype(&k_cavity_w<D, 8>) cavity_kernel(int occupancy) {
-  if (occupancy >= 16) return &k_cavity_w<D, 16>;
-  if (occupancy >= 12) return &k_cavity_w<D, 12>;
-  return &k_cavity_w<D, 8>;
+static decltype(&k_cavity_w<D, 8, 32>) cavity_kernel(int occupancy, int group) {
+  if (group == 16) return &k_cavity_w<D, 8, 16>;
+  if (occupancy >= 16) return &k_cavity_w<D, 16, 32>;
+  if (occupancy >= 12) return &k_cavity_w<D, 12, 32>;
+  return &k_cavity_w<D, 8, 32>;
 }
 
-// Second growth of large region q (one warp).
-template <int D>
+// Region growth by a whole thread block of NT threads (NT / (D+1) region
+// simplices x (D+1) facets per step), for the large regions: their
+// breadth-first front is wide, so a step of one block does the work of NT/32
+// warp steps at about the latency of one.  The rules are those of
+// grow_region: the same claims, the same boundary facets, the same statuses;
+// the per-step additions are placed by a scan over the block's warps.
+template <int D, int NT>
+__device__ __forceinline__ void grow_region_cta(const TriView<D>& T, int p, unsigned long long key, int* C, int* B,
+                                                int capC, int capB, int& nc_out, int& nbd_out, int& status_out,
+                                                unsigned long long& pbytes, unsigned long long& ptests) {
+  const unsigned FULL = 0xffffffffu;
+  constexpr int NW = NT / 32, PER = NT / (D + 1);
+  __shared__ int s_add[NW][3];                         // per warp: region, boundary, lost
+  __shared__ int s_first;                              // status after the located simplex
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  if (tid == 0) {
+    const int t0 = T.loc[p];
+    unsigned long long oc = atomicMax(&T.claimC[t0], key);
+    unsigned long long o = atomicMax(&T.claimA[t0], key);
+    s_first = (o > key || oc > key) ? CAND_LOST : CAND_OK;
+    C[0] = t0;
+    pbytes += sizeof(typename PT<D>::T) + 4 + 8 + 16 * (D + 1) + 16 + 4;
+  }
+  __syncthreads();
+  int status = s_first, nc = 1, nbd = 0, h = 0, nsteps = 0;
+  while (status == CAND_OK && h < nc) {                // block-uniform
+    const int nc0 = nc;
+    const int j = h + tid / (D + 1), i = tid % (D + 1);
+    const bool valid = tid < PER * (D + 1) && j < nc0;
+    bool addC = false, addB = false, lost = false, bad = false;
+    int t = -1, u = -1;
+    if (valid) {
+      t = C[j];
+      u = nb_simplex(*comp_ptr(T.tn, t, i));
+      if (!slot_ok(T, u)) {
+        bad = true;
+      } else {
+        const int4 vv = T.tv[u];
+        unsigned long long cC = *((volatile unsigned long long*)&T.claimC[u]);
+        pbytes += 16;
+        if (cC > key) {
+          lost = true;
+        } else if (cC != key) {
+          pbytes += 16 + (D + 1) * sizeof(typename PT<D>::T);
+          ptests++;
+          if (!verts_ok(T, vv)) {
+            bad = true;
+          } else {
+            int vt[4] = {vv.x, vv.y, vv.z, vv.w};
+            if (in_conflict_x(T.pts, T.xs, T.gid, vt, p, D)) {
+              unsigned long long o = atomicMax(&T.claimC[u], key);
+              unsigned long long o2 = atomicMax(&T.claimA[u], key);
+              if (o > key || o2 > key) {
+                lost = true;
+              } else if (o < key) {
+                addC = true;
+                pbytes += 16 + 4;
+              }
+            } else {
+              atomicMax(&T.claimA[u], key);
+              addB = true;
+              pbytes += 8 + 4;
+            }
+          }
+        }
+      }
+    }
+    if (bad) set_error(T.st, DT_E_INTERNAL, 10);
+    const unsigned mL = __ballot_sync(FULL, lost || bad), mC = __ballot_sync(FULL, addC),
+                   mB = __ballot_sync(FULL, addB);
+    if (lane == 0) { s_add[w][0] = __popc(mC); s_add[w][1] = __popc(mB); s_add[w][2] = mL != 0u; }
+    __syncthreads();
+    int offC = 0, offB = 0, nC = 0, nB = 0, anyL = 0;
+#pragma unroll
+    for (int q = 0; q < NW; q++) {
+      if (q < w) { offC += s_add[q][0]; offB += s_add[q][1]; }
+      nC += s_add[q][0]; nB += s_add[q][1]; anyL |= s_add[q][2];
+    }
+    if (anyL) {
+      status = CAND_LOST;
+    } else if (nc + nC > capC || nbd + nB > capB) {
+      status = CAND_OVER;
+    } else {
+      if (addC) C[nc + offC + __popc(mC & below)] = u;
+      if (addB) B[nbd + offB + __popc(mB & below)] = pack_nb(t, i);
+      nc += nC;
+      nbd += nB;
+      h = min(h + PER, nc0);
+    }
+    __syncthreads();                                   // list entries visible, s_add free again
+    nsteps++;
+  }
+  if (T.dbg && tid == 0) atomicAdd(&T.dbg[7], (unsigned long long)nsteps);
+  nc_out = nc;
+  nbd_out = nbd;
+  status_out = status;
+}
+
+// Threads per block of the large-region kernel (one block per region).
+constexpr int BIG_NT = 256;
+
+// Second growth of large region q (one block of NT threads, all of which call).
+template <int D, int NT>
 __device__ __forceinline__ void big_region(const TriView<D>& T, unsigned round, const CandScratch& S, int q) {
-  const int lane = threadIdx.x & 31;
   const int slot = S.biglist[q];
   const int p = S.cand[slot];
   const unsigned long long key = mkkey(round, p) | 1ull;   // second pass: see mkkey
@@ -576,29 +680,42 @@ __device__ __forceinline__ void big_region(const TriView<D>& T, unsigned round, 
   int* B = S.bigbnd + (int64_t)q * S.capBbig;
   unsigned long long pbytes = 0, ptests = 0;
   int nc, nbd, status;
-  grow_region<D, 32>(T, true, p, key, C, nullptr, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
-  region_stats<D, 32>(T, true, status, nc, pbytes, ptests);
-  if (lane == 0) {
+  grow_region_cta<D, NT>(T, p, key, C, B, S.capCbig, S.capBbig, nc, nbd, status, pbytes, ptests);
+  // counters: every warp adds its own lanes' bytes and tests, the first thread the region's
+  if (T.prof) {
+    for (int off = 16; off; off >>= 1) {
+      pbytes += __shfl_down_sync(0xffffffffu, pbytes, off);
+      ptests += __shfl_down_sync(0xffffffffu, ptests, off);
+    }
+    if ((threadIdx.x & 31) == 0) { atomicAdd(&T.prof[0], pbytes); atomicAdd(&T.prof[1], ptests); }
+  }
+  if (threadIdx.x == 0) {
+    if (T.dbg) {
+      if (status == CAND_OK) atomicAdd(&T.dbg[4], 1ull);
+      atomicAdd(&T.dbg[5], (unsigned long long)nc);
+    }
     if (status == CAND_OVER) atomicExch(&T.st->overflow_cav, 1);
     S.meta[slot] = make_int4(nc, nbd, status, q + 1);
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // Large regions: the nominees whose region outgrew the regular lists grow it
 // again into lists of capCbig / capBbig entries (their claims so far stand;
-// atomicMax makes the repeated claims harmless).
+// atomicMax makes the repeated claims harmless), one block per region.
 template <int D>
-__global__ void __launch_bounds__(128) k_cavity_big(TriView<D> T, unsigned round, CandScratch S, const EngCtl* ctl) {
+__global__ void __launch_bounds__(BIG_NT) k_cavity_big(TriView<D> T, unsigned round, CandScratch S, const EngCtl* ctl) {
   pdl_enter();
   if (ctl) {
     if (ctl->small || ctl->done) return;
     round = ctl->round;
   }
-  const int nwarp = (gridDim.x * blockDim.x) >> 5;
   const int nbig = min(*S.nbig, BIGCAP);
-  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nbig; q += nwarp) big_region<D>(T, round, S, q);
+  for (int q = blockIdx.x; q < nbig; q += gridDim.x) big_region<D, BIG_NT>(T, round, S, q);
 }
+
+// Blocks of the large-region kernel: at most one per region, at most one per SM.
+static inline unsigned big_grid(int sms) { return (unsigned)std::min(BIGCAP, std::max(sms, 1)); }
 
 // One warp per nominee: a nominee wins if no stronger nominee claimed any of
 // its region (claimA) or has any of its ring in its own region (claimC).
@@ -1145,7 +1262,7 @@ __global__ void __launch_bounds__(1024) k_small_rounds(TriView<D> T, EngCtl* ctl
     for (int slot = warp; slot < nn; slot += nw) cavity_slot<D>(T, round, S, nom, cnt + 8, slot);
     __syncthreads();
     const int nbig = min(vc[5], BIGCAP);
-    for (int q = warp; q < nbig; q += nw) big_region<D>(T, round, S, q);
+    for (int q = 0; q < nbig; q++) big_region<D, 1024>(T, round, S, q);   // the whole block, region by region
     __syncthreads();
     for (int slot = warp; slot < nn; slot += nw) insert_winner<D>(T, round, S, slot, cnt + 3);
     __syncthreads();
@@ -1341,7 +1458,8 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     std::string key;
     auto put = [&](const void* p, size_t nb) { key.append((const char*)p, nb); };
     const int dimk = D, pdlk = c->pdl_ok ? 1 : 0;
-    const void* ptrs[8] = {ctl, cnt, loffd, llist, nom, walk, c->status, cs};
+    const void* ptrs[9] = {ctl, cnt, loffd, llist, nom, walk, c->status, cs,
+                           (const void*)cavity_kernel<D>(c->cfg.cavity_occupancy, c->cfg.cavity_group)};
     const unsigned grids[4] = {gn, gr, ga, gw};
     put(&dimk, 4); put(&pdlk, 4); put(&T, sizeof(T)); put(&S, sizeof(S)); put(ptrs, sizeof(ptrs));
     put(grids, sizeof(grids)); put(&capCand, 4);
@@ -1388,13 +1506,13 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
         return lc;
       };
       cudaLaunchConfig_t l0 = cfg(1, 1024), l1 = cfg(ga, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128),
-                         l5 = cfg(gn, 256), l6 = cfg(gr, 128), l7 = cfg(1, 32), l8 = cfg(BIGCAP / 4, 128);
+                         l5 = cfg(gn, 256), l6 = cfg(gr, 128), l7 = cfg(1, 32), l8 = cfg(big_grid(c->sms), BIG_NT);
       l0.numAttrs = 0;   // the body's first node has no kernel before it inside the body
       cudaLaunchKernelEx(&l0, k_small_rounds<D>, T, ctl, cnt, loffd, (const int*)llist, nom, walk, S);
       cudaLaunchKernelEx(&l1, k_activate<D>, T, (const int*)llist, 0, (int*)nullptr, cnt + 0, 0u, (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, nom, cnt + 2, cnt + 8,
                          capCand, (const EngCtl*)ctl);
-      cudaLaunchKernelEx(&l3, cavity_kernel<D>(c->cfg.cavity_occupancy), T, (const int*)nom, (const int*)(cnt + 2), 0u, S,
+      cudaLaunchKernelEx(&l3, cavity_kernel<D>(c->cfg.cavity_occupancy, c->cfg.cavity_group), T, (const int*)nom, (const int*)(cnt + 2), 0u, S,
                          (const int*)(cnt + 8),
                          (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l8, k_cavity_big<D>, T, 0u, S, (const EngCtl*)ctl);
@@ -1677,9 +1795,11 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       cudaEventRecord(e, s);
       return (int)nev++;
     };
-    static const char* const knames[2][6] = {
-        {"k_nominate<2>", "k_cavity_w<2>", "k_insert_w<2>", "k_reloc_check<2>", "k_reloc_walk<2>", "k_activate<2>"},
-        {"k_nominate<3>", "k_cavity_w<3>", "k_insert_w<3>", "k_reloc_check<3>", "k_reloc_walk<3>", "k_activate<3>"}};
+    static const char* const knames[2][7] = {
+        {"k_nominate<2>", "k_cavity_w<2>", "k_insert_w<2>", "k_reloc_check<2>", "k_reloc_walk<2>", "k_activate<2>",
+         "k_cavity_big<2>"},
+        {"k_nominate<3>", "k_cavity_w<3>", "k_insert_w<3>", "k_reloc_check<3>", "k_reloc_walk<3>", "k_activate<3>",
+         "k_cavity_big<3>"}};
     // Profile and debug runs drive the rounds from the host (events and
     // checks between launches); otherwise one CUDA graph runs every round.
     const bool host_loop = prof || getenv("GDT_DEBUG") || getenv("GDT_CHECK");
@@ -1744,9 +1864,10 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
       k_nominate<D><<<gp, 256, (++c->launches, 0), s>>>(T, ain, cnt + 0, round, nom, cnt + 2, cnt + 8, capCand,
                                                         nullptr);
       ev[1] = mark();
-      cavity_kernel<D>(c->cfg.cavity_occupancy)<<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8,
+      cavity_kernel<D>(c->cfg.cavity_occupancy, c->cfg.cavity_group)<<<gw, 128, (++c->launches, 0), s>>>(T, nom, cnt + 2, round, S, cnt + 8,
                                                                                    nullptr);
-      k_cavity_big<D><<<BIGCAP / 4, 128, (++c->launches, 0), s>>>(T, round, S, nullptr);
+      const int evb = mark();
+      k_cavity_big<D><<<big_grid(c->sms), BIG_NT, (++c->launches, 0), s>>>(T, round, S, nullptr);
       ev[2] = mark();
       k_insert_w<D><<<gw, 128, (++c->launches, 0), s>>>(T, round, S, cnt + 2, cnt + 3, nullptr);
       ev[3] = mark();
@@ -1757,18 +1878,25 @@ static int engine_run_t(dt_ctx* c, EngineRun& run, const void* pts, const int* g
                                                                                       nullptr);
       ev[5] = mark();
       for (int q = 0; q < 5; q++)
-        if (ev[q] >= 0 && ev[q + 1] >= 0) recs.push_back({ev[q], ev[q + 1], q, round});
+        if (ev[q] >= 0 && ev[q + 1] >= 0) {
+          if (q == 1 && evb >= 0) {                    // region growth, then the large regions
+            recs.push_back({ev[1], evb, 1, round});
+            recs.push_back({evb, ev[2], 6, round});
+          } else {
+            recs.push_back({ev[q], ev[q + 1], q, round});
+          }
+        }
       if (getenv("GDT_DEBUG")) {
         int hc[5];
-        unsigned long long hd[7];
+        unsigned long long hd[8];
         cudaMemcpyAsync(hc, cnt, 20, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(hd, T.dbg, 56, cudaMemcpyDeviceToHost, s);
-        cudaMemsetAsync(T.dbg, 0, 56, s);
+        cudaMemcpyAsync(hd, T.dbg, 64, cudaMemcpyDeviceToHost, s);
+        cudaMemsetAsync(T.dbg, 0, 64, s);
         cudaStreamSynchronize(s);
         fprintf(stderr,
                 "round %u nact %d cand %d win %d walk %d steps %llu max %llu act_steps %llu act_max %llu "
-                "complete %llu grown %llu large %llu\n",
-                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3], hd[4], hd[5], hd[6]);
+                "complete %llu grown %llu large %llu grow_steps %llu\n",
+                round, hc[0], hc[2], hc[3], hc[4], hd[0], hd[1], hd[2], hd[3], hd[4], hd[5], hd[6], hd[7]);
       }
       k_move_count<<<1, 1, (++c->launches, 0), s>>>(cnt + 0, cnt + 1);
       std::swap(ain, aout);
@@ -2309,13 +2437,13 @@ static int stream_graph(dt_ctx* c, StreamState& st, cudaGraphConditionalHandle* 
     EngCtl* ctl = (EngCtl*)st.ctl;
     int* cnt = st.cnt;
     cudaLaunchConfig_t l1 = cfg(gr, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128), l5 = cfg(gn, 256),
-                       l6 = cfg(gr, 128), l7 = cfg(1, tb), l8 = cfg(BIGCAP / 4, 128);
+                       l6 = cfg(gr, 128), l7 = cfg(1, tb), l8 = cfg(big_grid(c->sms), BIG_NT);
     l1.numAttrs = 0;
     cudaLaunchKernelEx(&l1, k_stream_activate<D>, T, (const int*)st.llist, (const int*)st.seg, J, cnt + 0,
                        (const EngCtl*)ctl);
     cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, st.nom, cnt + 2, cnt + 8,
                        capCand, (const EngCtl*)ctl);
-    cudaLaunchKernelEx(&l3, cavity_kernel<D>(c->cfg.cavity_occupancy), T, (const int*)st.nom, (const int*)(cnt + 2), 0u,
+    cudaLaunchKernelEx(&l3, cavity_kernel<D>(c->cfg.cavity_occupancy, c->cfg.cavity_group), T, (const int*)st.nom, (const int*)(cnt + 2), 0u,
                        st.S,
                        (const int*)(cnt + 8), (const EngCtl*)ctl);
     cudaLaunchKernelEx(&l8, k_cavity_big<D>, T, 0u, st.S, (const EngCtl*)ctl);
