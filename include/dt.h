@@ -137,6 +137,9 @@ typedef struct dt_config {
                             one warp per nominee; the kernels loop over the nominees); 0 = automatic (16) */
   int cavity_occupancy;  /* resident blocks per SM the region-growth kernel is compiled for: 8, 12 or 16
                             (registers per thread capped at 64, 40, 32); 0 = automatic (8) */
+  int cavity_group;      /* lanes of the region-growth kernel per nominee: 32 (one warp, 8 region
+                            simplices per step in 3D) or 16 (two nominees per warp, 4 per step);
+                            0 = automatic (32) */
 } dt_config;
 
 typedef struct dt_stats {

@@ -54,7 +54,8 @@ class Config(ctypes.Structure):
                 ("partition_init", ctypes.c_int), ("recursive", ctypes.c_int),
                 ("active_ratio", ctypes.c_int), ("nominate_rings", ctypes.c_int), ("partitioner", ctypes.c_int),
                 ("round_limit", ctypes.c_int), ("walk_limit", ctypes.c_int), ("arena_factor", ctypes.c_int),
-                ("cavity_blocks", ctypes.c_int), ("cavity_occupancy", ctypes.c_int)]
+                ("cavity_blocks", ctypes.c_int), ("cavity_occupancy", ctypes.c_int),
+                ("cavity_group", ctypes.c_int)]
 
 
 class KernelProfile(ctypes.Structure):

@@ -46,7 +46,8 @@ static bool cfg_valid(const dt_config* c) {
          c->partitioner == DT_PART_MULTILEVEL) && c->round_limit >= 0 && c->walk_limit >= 0 &&
          c->arena_factor >= 0 && c->arena_factor <= 1024 && c->cavity_blocks >= 0 && c->cavity_blocks <= 64 &&
          (c->cavity_occupancy == 0 || c->cavity_occupancy == 8 || c->cavity_occupancy == 12 ||
-          c->cavity_occupancy == 16);
+          c->cavity_occupancy == 16) &&
+         (c->cavity_group == 0 || c->cavity_group == 16 || c->cavity_group == 32);
 }
 
 extern "C" int dt_create(dt_ctx** out, int device, void* cuda_stream, const dt_config* cfg) {

@@ -156,7 +156,7 @@ def test_single_block_rounds_match_oracle(tri, D, kind):
         assert np.array_equal(got, want), sr
 
 
-@pytest.mark.parametrize("cfg", [dict(cavity_occupancy=12), dict(cavity_occupancy=16),
+@pytest.mark.parametrize("cfg", [dict(cavity_occupancy=12), dict(cavity_occupancy=16), dict(cavity_group=16),
                                  dict(nominate_rings=2, cavity_blocks=8), dict(active_ratio=25)])
 def test_schedule_knobs_match_oracle(tri, cfg):
     """Launch shapes and schedules change which nominees win a round, never
