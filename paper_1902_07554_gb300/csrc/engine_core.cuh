@@ -1457,11 +1457,11 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     // every parameter baked into the graph: an equal key means an equal graph
     std::string key;
     auto put = [&](const void* p, size_t nb) { key.append((const char*)p, nb); };
-    const int dimk = D, pdlk = c->pdl_ok ? 1 : 0;
+    const int dimk = D, pdlk = c->pdl_ok ? 1 : 0, smallk = c->cfg.small_rounds > 0 ? 1 : 0;
     const void* ptrs[9] = {ctl, cnt, loffd, llist, nom, walk, c->status, cs,
                            (const void*)cavity_kernel<D>(c->cfg.cavity_occupancy, c->cfg.cavity_group)};
     const unsigned grids[4] = {gn, gr, ga, gw};
-    put(&dimk, 4); put(&pdlk, 4); put(&T, sizeof(T)); put(&S, sizeof(S)); put(ptrs, sizeof(ptrs));
+    put(&dimk, 4); put(&pdlk, 4); put(&smallk, 4); put(&T, sizeof(T)); put(&S, sizeof(S)); put(ptrs, sizeof(ptrs));
     put(grids, sizeof(grids)); put(&capCand, 4);
     cudaGraph_t g = nullptr;
     cudaGraphExec_t gx = nullptr;
@@ -1507,8 +1507,14 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
       };
       cudaLaunchConfig_t l0 = cfg(1, 1024), l1 = cfg(ga, 128), l2 = cfg(gn, 256), l3 = cfg(gw, 128), l4 = cfg(gw, 128),
                          l5 = cfg(gn, 256), l6 = cfg(gr, 128), l7 = cfg(1, 32), l8 = cfg(big_grid(c->sms), BIG_NT);
-      l0.numAttrs = 0;   // the body's first node has no kernel before it inside the body
-      cudaLaunchKernelEx(&l0, k_small_rounds<D>, T, ctl, cnt, loffd, (const int*)llist, nom, walk, S);
+      // the body's first node has no kernel before it inside the body; the
+      // single-block rounds are a node only when they are enabled
+      if (c->cfg.small_rounds > 0) {
+        l0.numAttrs = 0;
+        cudaLaunchKernelEx(&l0, k_small_rounds<D>, T, ctl, cnt, loffd, (const int*)llist, nom, walk, S);
+      } else {
+        l1.numAttrs = 0;
+      }
       cudaLaunchKernelEx(&l1, k_activate<D>, T, (const int*)llist, 0, (int*)nullptr, cnt + 0, 0u, (const EngCtl*)ctl);
       cudaLaunchKernelEx(&l2, k_nominate<D>, T, (const int*)nullptr, (const int*)(cnt + 0), 0u, nom, cnt + 2, cnt + 8,
                          capCand, (const EngCtl*)ctl);
@@ -1557,7 +1563,7 @@ static int graph_rounds(dt_ctx* c, TriView<D>& T, EngineRun& run, int64_t npts, 
     CUDA_OK(cudaMemcpyAsync(&h1, ctl, sizeof(EngCtl), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaMemcpyAsync(c->status_host, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
-    c->launches += 1 + 10 * (int64_t)(h1.round - r0 + 1);
+    c->launches += 1 + (c->cfg.small_rounds > 0 ? 9 : 8) * (int64_t)(h1.round - r0 + 1);   // body nodes per round
     if (h1.done == 3 && c->status_host->overflow_cav && grow < 8) {
       // cavities outgrew their scratch: twice the room, same state
       CUDA_OK(cudaMemsetAsync(&c->status->overflow_cav, 0, 4, s));
