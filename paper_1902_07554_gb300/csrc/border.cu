@@ -577,8 +577,17 @@ __global__ void k_border(const typename PT<D>::T* P, BorderArgs A) {
   if (g >= 0) {
     ghost_halfspace<D>(P, v, g, S);
     hit = gridded ? grid_query<D>(A.G, S, others, points) : bbox_query<D>(A.boxes, A.k, S, others, i);
-  } else if (gridded && circumball_f32<D>(A.xs, A.xo, v, S) && !grid_query<D>(A.G, S, others, points)) {
-    hit = false;   // even the larger FP32 ball meets no other partition
+  } else if (gridded && circumball_f32<D>(A.xs, A.xo, v, S)) {
+    if (!grid_query<D>(A.G, S, others, points)) {
+      hit = false;   // even the larger FP32 ball meets no other partition
+    } else if (!points) {
+      // the FP32 ball contains the FP64 one, so a hit is a (slightly larger)
+      // superset of the grid test's border: no FP64 ball for the grid primitive
+      hit = true;
+    } else {
+      // the point test decides point by point: take the tighter FP64 ball
+      hit = circumball<D>(P, v, S) ? grid_query<D>(A.G, S, others, points) : true;
+    }
   } else if (!circumball<D>(P, v, S)) {
     hit = true;
   } else {
