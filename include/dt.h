@@ -366,7 +366,11 @@ DT_API int dt_release_job(dt_ctx* ctx, uint64_t job);
  * 1024 jobs resident at once.  One stream per context; it holds about
  * (arena_factor x 48 + 100) bytes per point of capacity plus fixed scratch
  * (dt_stream_get_info reports the total).  DT_E_NOMEM if the device cannot
- * hold it. */
+ * hold it.  The rounds of a stream are numbered over its whole life (the
+ * number orders its claims, which are not cleared between jobs), so one
+ * stream serves at most 2^31 - 1 insertion rounds, about nine days at the
+ * ~2,800 rounds per second of a busy 3D serving load; close and reopen it
+ * before that. */
 DT_API int dt_stream_open(dt_ctx* ctx, int dim, int64_t capacity, int max_jobs);
 
 /* Queues a job: n points (n x dim float64, HOST memory, copied).  May be
